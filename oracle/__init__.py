@@ -1,0 +1,348 @@
+"""CPU FP64 oracle for the frozen full-metric Eikonal tangent transport (arxiv 2609.14982).
+
+TEST INFRASTRUCTURE ONLY: only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg import this package.  It shares no code with the CUDA
+library; both take their inputs from ``paper_2609_14982_b300.workloads``.
+
+What it computes (paper sections in brackets):
+  * metric J = dx/dxi by finite differences, G = J^-1 J^-T, mu_G      [Sec. 2.2, Eq. muG]
+  * face-based upwind rows A = I - W and the calibration c^(s)        [Sec. 3.1-3.2]
+  * dependency graph, SCCs (Tarjan), Kahn residual                    [Sec. 3.3-3.5, 4.1]
+  * canonical condensation order and levels (longest path)            [Sec. 4.1]
+  * dense partial-pivot LU of every nontrivial SCC block              [Sec. 4.3]
+  * block traversals A^-1 q and A^-T r                                 [Prop. 3, Sec. 4.3]
+  * the plain definition of the same solves: assembled sparse A and a
+    library direct solve (numpy dense / SciPy sparse LU)              [Eq. transport-system]
+  * J = P A^-1 C M and J^T = M^T C^T A^-T P^T, summed over sources     [Sec. 4.4]
+  * directional sweeping (Gauss-Seidel over 2^D orderings)            [Sec. 3.6]
+
+Where the paper leaves a detail open the oracle takes one stated reading (face
+averages, boundary stencils, canonical order); those readings are pinned by the
+paper's printed Tables 1-3 in tests/test_oracle_*.py.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_pd = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_pl = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_pi = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_pc = np.ctypeslib.ndpointer(dtype=np.int8, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c (gcc, FP64, no contraction of multiply-adds)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        I, Lg, D = C.c_int, C.c_long, C.c_double
+        L.or_metric.argtypes = [I, _pi, _pd, _pd, _pd, _pd, _pd]
+        L.or_grad.argtypes = [I, _pi, _pd, _pd, _pd]
+        L.or_assemble.argtypes = [I, _pi, _pd, _pd, _pd, _pd, _pd, Lg, _pl, _pi, _pd, _pd, _pd, _pi]
+        L.or_assemble.restype = Lg
+        L.or_scc.argtypes = [Lg, _pl, _pi, _pi]
+        L.or_scc.restype = Lg
+        L.or_levels.argtypes = [Lg, _pl, _pi, _pi, _pi, _pi, _pl, _pl, C.POINTER(Lg)]
+        L.or_levels.restype = Lg
+        L.or_lu.argtypes = [I, _pd, _pi]
+        L.or_lu_solve.argtypes = [I, _pd, _pi, _pd]
+        L.or_lu_solve_T.argtypes = [I, _pd, _pi, _pd]
+        L.or_btf_solve.argtypes = [Lg, _pl, _pi, _pd, _pi, Lg, _pl, _pl, _pd, _pi, _pl, _pd, _pd, _pd]
+        L.or_btf_solve_T.argtypes = [Lg, _pl, _pi, _pd, _pi, Lg, _pl, _pl, _pd, _pi, _pl, _pd, _pd, _pd]
+        L.or_sweep.argtypes = [I, _pi, I, _pl, _pi, _pd, _pd, _pd, D, Lg]
+        L.or_sweep.restype = Lg
+        L.or_kahn_residual.argtypes = [Lg, _pl, _pi, _pc]
+        L.or_kahn_residual.restype = Lg
+        _lib = L
+    return _lib
+
+
+def _n(grid):
+    return np.ascontiguousarray(grid.n, dtype=np.int32), np.ascontiguousarray(grid.dxi, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------- metric
+def metric(grid):
+    """Sec. 2.2: returns (J [N,d,d], G [N,d,d], det J [N])."""
+    n, dxi = _n(grid)
+    N, d = grid.N, grid.ndim
+    J = np.zeros((N, d, d))
+    G = np.zeros((N, d, d))
+    det = np.zeros(N)
+    if lib().or_metric(d, n, dxi, np.ascontiguousarray(grid.xyz), J.reshape(-1), G.reshape(-1), det) != 0:
+        raise ValueError("grid needs at least 3 nodes per dimension")
+    return J, G, det
+
+
+def mu_G(G: np.ndarray) -> float:
+    """Eq. (muG): max over nodes and index pairs of |G_ab| / sqrt(G_aa G_bb)."""
+    d = G.shape[1]
+    best = 0.0
+    for a in range(d):
+        for b in range(a + 1, d):
+            best = max(best, float(np.max(np.abs(G[:, a, b]) / np.sqrt(G[:, a, a] * G[:, b, b]))))
+    return best
+
+
+def grad(grid, f: np.ndarray) -> np.ndarray:
+    n, dxi = _n(grid)
+    g = np.zeros((grid.N, grid.ndim))
+    lib().or_grad(grid.ndim, n, dxi, np.ascontiguousarray(f, dtype=np.float64), g.reshape(-1))
+    return g
+
+
+# --------------------------------------------------------------------------- tangent
+@dataclass
+class Tangent:
+    """The frozen per-source state S_alpha = {T, A, graph, Pi, LU factors} (Sec. 4.3)."""
+    N: int
+    src: int
+    row_ptr: np.ndarray     # gather form: upstream j of row i at col[row_ptr[i]:row_ptr[i+1]]
+    col: np.ndarray
+    c: np.ndarray           # coupling magnitudes c_ij
+    w: np.ndarray           # normalized weights w_ij
+    cs: np.ndarray          # calibration c^(s)_i (0 on the seed row)
+    row_type: np.ndarray    # 0 interior, 1 seed, 2 identity (no upstream face)
+    label: np.ndarray = None      # SCC label = smallest node of the component
+    level: np.ndarray = None      # level of the node's component
+    perm: np.ndarray = None       # position -> node (canonical order)
+    comp_ptr: np.ndarray = None
+    level_ptr: np.ndarray = None
+    ncomp: int = 0
+    nlev: int = 0
+    lu_off: np.ndarray = None
+    lu: np.ndarray = None
+    piv: np.ndarray = None
+    piv_off: np.ndarray = None
+    cptr: np.ndarray = None       # column (transpose) form
+    crow: np.ndarray = None
+    cw: np.ndarray = None
+
+    def A(self):
+        """Assembled sparse A = I - W (Eq. transport-system)."""
+        import scipy.sparse as sp
+        rows = np.repeat(np.arange(self.N), np.diff(self.row_ptr))
+        W = sp.csr_matrix((self.w, (rows, self.col)), shape=(self.N, self.N))
+        return (sp.identity(self.N, format="csr") - W).tocsr()
+
+    def edges(self):
+        """(j, i) pairs of the dependency graph: edge j -> i iff w_ij > 0 (Sec. 3.3)."""
+        rows = np.repeat(np.arange(self.N), np.diff(self.row_ptr))
+        return self.col.astype(np.int64), rows
+
+    # -- structure statistics (Sec. 5.2, Eq. graph-fractions)
+    def scc_sizes(self) -> np.ndarray:
+        _, counts = np.unique(self.label, return_counts=True)
+        return counts
+
+    def kahn_unresolved(self) -> int:
+        rem = np.zeros(self.N, dtype=np.int8)
+        return int(lib().or_kahn_residual(self.N, self.row_ptr, self.col, rem))
+
+    def kahn_removed(self) -> np.ndarray:
+        rem = np.zeros(self.N, dtype=np.int8)
+        lib().or_kahn_residual(self.N, self.row_ptr, self.col, rem)
+        return rem.astype(bool)
+
+
+def assemble(grid, G, T, s, src) -> Tangent:
+    """Sec. 3.1-3.2: upwind rows and calibration for one source state T."""
+    n, dxi = _n(grid)
+    N = grid.N
+    gT = grad(grid, T)
+    row_ptr = np.zeros(N + 1, dtype=np.int64)
+    cap = 2 * grid.ndim * N
+    col = np.zeros(cap, dtype=np.int32)
+    cw = np.zeros(cap)
+    w = np.zeros(cap)
+    cs = np.zeros(N)
+    rt = np.zeros(N, dtype=np.int32)
+    nnz = lib().or_assemble(grid.ndim, n, dxi, np.ascontiguousarray(G.reshape(-1)), gT.reshape(-1),
+                            np.ascontiguousarray(T, dtype=np.float64), np.ascontiguousarray(s, dtype=np.float64),
+                            int(src), row_ptr, col, cw, w, cs, rt)
+    if nnz < 0:
+        raise ValueError("assembly failed")
+    return Tangent(N, int(src), row_ptr, col[:nnz].copy(), cw[:nnz].copy(), w[:nnz].copy(), cs, rt)
+
+
+def condense(t: Tangent) -> Tangent:
+    """Sec. 4.1: SCC labels, canonical levels/order, and LU factors of the nontrivial blocks."""
+    L = lib()
+    N = t.N
+    label = np.zeros(N, dtype=np.int32)
+    L.or_scc(N, t.row_ptr, t.col, label)
+    level = np.zeros(N, dtype=np.int32)
+    perm = np.zeros(N, dtype=np.int32)
+    comp_ptr = np.zeros(N + 1, dtype=np.int64)
+    level_ptr = np.zeros(N + 1, dtype=np.int64)
+    nc = C.c_long(0)
+    nlev = L.or_levels(N, t.row_ptr, t.col, label, level, perm, comp_ptr, level_ptr, C.byref(nc))
+    if nlev < 0:
+        raise RuntimeError("condensation is not acyclic" if nlev == -1 else "grid too large for the oracle key")
+    ncomp = nc.value
+    t.label, t.level, t.perm = label, level, perm
+    t.comp_ptr = comp_ptr[:ncomp + 1].copy()
+    t.level_ptr = level_ptr[:nlev + 1].copy()
+    t.ncomp, t.nlev = ncomp, int(nlev)
+    # LU of nontrivial blocks (nodes ascending inside a block)
+    sizes = np.diff(t.comp_ptr)
+    lu_off = np.full(ncomp, -1, dtype=np.int64)
+    piv_off = np.full(ncomp, -1, dtype=np.int64)
+    blocks = np.nonzero(sizes > 1)[0]
+    tot = int(np.sum(sizes[blocks].astype(np.int64) ** 2))
+    lu = np.zeros(max(tot, 1))
+    piv = np.zeros(max(int(np.sum(sizes[blocks])), 1), dtype=np.int32)
+    o = po = 0
+    for c in blocks:
+        k = int(sizes[c])
+        nodes = perm[t.comp_ptr[c]:t.comp_ptr[c + 1]]
+        Ac = block_matrix(t, nodes)
+        a = np.ascontiguousarray(Ac.reshape(-1))
+        p = np.zeros(k, dtype=np.int32)
+        if L.or_lu(k, a, p) != 0:
+            raise np.linalg.LinAlgError(f"singular SCC block of size {k}")
+        lu[o:o + k * k] = a
+        piv[po:po + k] = p
+        lu_off[c] = o
+        piv_off[c] = po
+        o += k * k
+        po += k
+    t.lu_off, t.lu, t.piv, t.piv_off = lu_off, lu, piv, piv_off
+    # transpose (column) form
+    rows = np.repeat(np.arange(N, dtype=np.int32), np.diff(t.row_ptr))
+    order = np.argsort(t.col, kind="stable")
+    t.crow = rows[order].astype(np.int32)
+    t.cw = t.w[order].copy()
+    cnt = np.bincount(t.col, minlength=N)
+    t.cptr = np.zeros(N + 1, dtype=np.int64)
+    t.cptr[1:] = np.cumsum(cnt)
+    return t
+
+
+def block_matrix(t: Tangent, nodes: np.ndarray) -> np.ndarray:
+    """A_C = I - W_CC for a component (nodes ascending), Sec. 4.2."""
+    k = len(nodes)
+    where = {int(v): a for a, v in enumerate(nodes)}
+    Ac = np.eye(k)
+    for a, i in enumerate(nodes):
+        for e in range(t.row_ptr[i], t.row_ptr[i + 1]):
+            b = where.get(int(t.col[e]))
+            if b is not None:
+                Ac[a, b] -= t.w[e]
+    return Ac
+
+
+def build_tangent(grid, G, T, s, src) -> Tangent:
+    return condense(assemble(grid, G, T, s, src))
+
+
+# --------------------------------------------------------------------------- solves
+def solve(t: Tangent, q: np.ndarray) -> np.ndarray:
+    """x = A^-1 q by block traversal (Prop. 3).  q: [N] or [N, R]."""
+    q = np.asarray(q, dtype=np.float64)
+    if q.ndim == 2:
+        return np.stack([solve(t, q[:, r]) for r in range(q.shape[1])], axis=1)
+    x = np.zeros(t.N)
+    work = np.zeros(max(int(np.max(np.diff(t.comp_ptr))), 1))
+    lib().or_btf_solve(t.N, t.row_ptr, t.col, t.w, t.perm, t.ncomp, t.comp_ptr, t.lu_off, t.lu,
+                       t.piv, t.piv_off, np.ascontiguousarray(q), x, work)
+    return x
+
+
+def solve_T(t: Tangent, r: np.ndarray) -> np.ndarray:
+    """lam = A^-T r by reverse block traversal with U^T, L^T, P^T (Sec. 4.3)."""
+    r = np.asarray(r, dtype=np.float64)
+    if r.ndim == 2:
+        return np.stack([solve_T(t, r[:, k]) for k in range(r.shape[1])], axis=1)
+    lam = np.zeros(t.N)
+    work = np.zeros(max(int(np.max(np.diff(t.comp_ptr))), 1))
+    lib().or_btf_solve_T(t.N, t.cptr, t.crow, t.cw, t.perm, t.ncomp, t.comp_ptr, t.lu_off, t.lu,
+                         t.piv, t.piv_off, np.ascontiguousarray(r), lam, work)
+    return lam
+
+
+def direct_solve(t: Tangent, q: np.ndarray, transpose: bool = False) -> np.ndarray:
+    """The plain definition: assemble A and call a library direct solver."""
+    A = t.A()
+    if transpose:
+        A = A.T.tocsc()
+    if t.N <= 3000:
+        return np.linalg.solve(A.toarray(), q)
+    import scipy.sparse.linalg as spla
+    return spla.splu(A.tocsc()).solve(np.asarray(q, dtype=np.float64))
+
+
+def sweep(grid, t: Tangent, b: np.ndarray, transpose=False, tol=1e-12, max_cycles=100000):
+    """Sec. 3.6: directional Gauss-Seidel sweeping; returns (x, cycles)."""
+    n, _ = _n(grid)
+    x = np.zeros(t.N)
+    if transpose:
+        cyc = lib().or_sweep(grid.ndim, n, 1, t.cptr, t.crow, t.cw, np.ascontiguousarray(b, dtype=np.float64),
+                             x, tol, max_cycles)
+    else:
+        cyc = lib().or_sweep(grid.ndim, n, 0, t.row_ptr, t.col, t.w, np.ascontiguousarray(b, dtype=np.float64),
+                             x, tol, max_cycles)
+    return x, int(cyc)
+
+
+# --------------------------------------------------------------------------- maps and J
+MODEL_SLOWNESS, MODEL_VELOCITY, MODEL_RELATIVE = 0, 1, 2
+
+
+def model_factor(s: np.ndarray, model: int) -> np.ndarray:
+    """M (Sec. 2.3): ds = p (slowness), ds = -s^2 dv (velocity), ds = -s m (relative)."""
+    if model == MODEL_SLOWNESS:
+        return np.ones_like(s)
+    if model == MODEL_VELOCITY:
+        return -s * s
+    return -s
+
+
+def J(tans, s, rec, p, model=MODEL_SLOWNESS, shared=True, solver=solve):
+    """Eq. (source-jacobian) with D = 0: J_a p = P A_a^-1 C_a M p for every source.
+    p: [N, R] (shared model) or [S, N, R]; rec: [n_rec] node indices.
+    Returns d_rec [S, n_rec, R]."""
+    m = model_factor(s, model)
+    out = []
+    for a, t in enumerate(tans):
+        pa = p if shared else p[a]
+        pa = pa if pa.ndim == 2 else pa[:, None]
+        ds = m[:, None] * pa
+        q = t.cs[:, None] * ds
+        dT = solver(t, q)
+        out.append(dT[np.asarray(rec)])
+    return np.stack(out)
+
+
+def JT(tans, s, rec, y, model=MODEL_SLOWNESS, sum_sources=True, solver=solve_T):
+    """Eq. (source-transpose) with D = 0: J_a^T y_a = M^T C^T A_a^-T P^T y_a, summed over
+    sources when sum_sources.  y: [S, n_rec, R].  Returns [N, R] or [S, N, R]."""
+    m = model_factor(s, model)
+    outs = []
+    for a, t in enumerate(tans):
+        r = np.zeros((t.N, y.shape[2]))
+        np.add.at(r, np.asarray(rec), y[a])
+        lam = solver(t, r)
+        outs.append(m[:, None] * t.cs[:, None] * lam)
+    outs = np.stack(outs)
+    return outs.sum(axis=0) if sum_sources else outs
