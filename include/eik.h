@@ -1,0 +1,238 @@
+/*
+ * libeik: frozen full-metric Eikonal tangent transport on one B300 (sm_103a).
+ *
+ * The library applies A^-1 and A^-T of the frozen linearized transport (Sec. 3.1,
+ * Eq. transport-system, A = I - W) inside the Jacobian actions J p and J^T y
+ * (Sec. 4.4, Eqs. source-jacobian and source-transpose) as a block-triangular solve
+ * over the SCC condensation of the upwind dependency graph (Sec. 4.1, Eq. block-form,
+ * Prop. 3).  All work runs in the library's own CUDA kernels.
+ *
+ * Conventions
+ *   Grid: logical dims 3-D (xi, eta, zeta) or 2-D (xi, zeta); zeta last, zeta = 0 is
+ *     the top surface.  Node (i,j,k) has linear index (i*n1 + j)*n2 + k (2-D: i*n1 + k);
+ *     N = product of n.
+ *   Vectors: right-hand-side index fastest.  A per-source field is [S][N][R]; a model
+ *     vector shared by all sources is [N][R]; receiver data is [S][n_rec][R].
+ *   Pointers documented "device" must be device memory of the current device; "host"
+ *     pointers are read before the call returns.
+ *   Streams: every call is asynchronous on `stream` (a cudaStream_t) unless stated;
+ *     NULL means the legacy default stream.
+ *   Ownership: the caller owns every buffer it passes.  The library owns an
+ *     eik_tangent (structure, weights, factors, workspaces) until tangent_free.
+ *   Errors: every call returns EIK_OK (0) or a negative eik_status and never throws
+ *     across the ABI; eik_last_error() gives a thread-local message.  Faults detected
+ *     on the device (a singular block, a wait that timed out) are latched in the
+ *     tangent and returned by tangent_status().
+ */
+#ifndef EIK_H
+#define EIK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *eik_stream;      /* same object as cudaStream_t */
+
+typedef enum {
+    EIK_OK = 0,
+    EIK_ERR_INVALID = -1,          /* bad argument (sizes, null pointers, duplicate receivers) */
+    EIK_ERR_OOM = -2,              /* device allocation failed */
+    EIK_ERR_SINGULAR_BLOCK = -3,   /* an SCC block had a pivot below eik_opts.lu_pivot_tol */
+    EIK_ERR_NOT_CONVERGED = -4,    /* iterative solve (eik_forward, sweeping) hit its limit */
+    EIK_ERR_TIMEOUT = -5,          /* a bounded device-side wait ran out */
+    EIK_ERR_CUDA = -6,             /* CUDA runtime error */
+    EIK_ERR_CYCLE = -7             /* internal: condensation not acyclic (never expected) */
+} eik_status;
+
+typedef enum { EIK_F64 = 0, EIK_F32 = 1 } eik_dtype;
+
+/* Model map M (Sec. 2.3): ds = p (slowness), ds = -s^2 dv (velocity), ds = -s m
+ * (relative velocity perturbation m = dv/v). */
+typedef enum { EIK_MODEL_SLOWNESS = 0, EIK_MODEL_VELOCITY = 1, EIK_MODEL_RELATIVE = 2 } eik_model;
+
+/* Traversal schedule of tangent_apply / tangent_apply_T. */
+typedef enum {
+    EIK_SCHED_PERSISTENT = 0,      /* one persistent launch, device level queue, bounded waits */
+    EIK_SCHED_LEVELS = 1           /* one launch per level (host loop, graph-capturable) */
+} eik_schedule;
+
+typedef struct {
+    int ndim;             /* 2 or 3 */
+    int n[3];             /* nodes per logical dimension, each >= 3 */
+    double dxi[3];        /* logical spacing per dimension (> 0) */
+    const double *xyz;    /* device [N][ndim] physical coordinates (x[, y], z) */
+} eik_grid;
+
+typedef struct {
+    int model;                 /* eik_model, used by tangent_build for the M map */
+    double lu_pivot_tol;       /* |pivot| below this marks a block singular (default 1e-13) */
+    int schedule;              /* eik_schedule (default persistent) */
+    int threads;               /* CTA size of the traversal kernels (default 256) */
+    int chunk;                 /* singleton nodes per work item (default 0 = auto) */
+    int ctas_per_sm;           /* persistent grid = SMs x this (default 0 = occupancy) */
+    double wait_timeout_s;     /* bound on any device-side wait (default 2 s) */
+    /* eik_forward */
+    double eik_tol;            /* stop when max |d tau| < eik_tol over a cycle (default 1e-12) */
+    int eik_max_cycles;        /* (default 2000) */
+    double eik_src_radius;     /* tau = 1 for |x - x_src| <= radius * max(dxi) (default 1.0) */
+    /* sweeping baseline */
+    double sweep_tol;          /* max |dx| <= sweep_tol * max |x| over one cycle (default 1e-12) */
+    int sweep_max_cycles;      /* (default 10000) */
+} eik_opts;
+
+typedef struct {
+    int64_t nodes;             /* N */
+    int64_t edges;             /* dependencies w_ij > 0 */
+    int64_t components;        /* SCCs (singletons included) */
+    int64_t nontrivial;        /* SCCs with >= 2 nodes */
+    int64_t cyclic_nodes;      /* nodes in nontrivial SCCs */
+    int64_t largest;           /* largest SCC */
+    int64_t levels;            /* levels of the condensation DAG (longest path + 1) */
+    int64_t max_level_width;   /* most nodes in one level */
+    int64_t identity_rows;     /* non-seed rows without an upstream face */
+    int64_t lu_doubles;        /* FP64 words held by block factors */
+} eik_stats;
+
+/* Fill opts with the defaults listed above. */
+void eik_opts_default(eik_opts *opts);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char *eik_last_error(void);
+
+/* Library build string (architecture, version). */
+const char *eik_version(void);
+
+/*
+ * eik_forward -- first-arrival traveltimes T_a for S point sources (Sec. 2.1,
+ * Eq. eikonal with the point-source factorization T = T0 tau, and Sec. 2.2,
+ * Eq. metric-eikonal).  The paper cites its state solver (FTDEE) without giving it;
+ * this call solves the factored full-metric equation with first-order Lax-Friedrichs
+ * sweeping to a discrete fixed point (tau = 1 near the source).
+ *   g        grid (xyz device)
+ *   s        device [N] slowness
+ *   S        number of sources
+ *   src_node host [S] node index of each source
+ *   T        device [S][N] output (seconds in the grid's units times slowness units)
+ *   cycles   host, optional: number of sweep cycles used
+ * Returns EIK_ERR_NOT_CONVERGED when eik_max_cycles is reached (T holds the last
+ * iterate).  Synchronizes the stream once per cycle to test convergence.
+ */
+int eik_forward(const eik_grid *g, const double *s, int S, const int *src_node,
+                double *T, const eik_opts *opts, int *cycles, eik_stream stream);
+
+typedef struct eik_tangent eik_tangent;
+
+/*
+ * tangent_build -- Phase I of Algorithm 1 (Sec. 4.6, Alg. 1 steps 7-10) for S sources:
+ * face-based upwind rows A_a = I - W_a (Sec. 3.1), calibration c^(s) = (A T)/s
+ * (Sec. 3.2), dependency graph (Sec. 3.3), SCCs and the canonical level order of the
+ * condensation DAG (Sec. 4.1), dense LU of every nontrivial SCC block (Sec. 4.3).
+ *   T        device [S][N] frozen traveltimes (e.g. from eik_forward)
+ *   s        device [N] slowness
+ *   src_node host [S] seed node of each source (its row is the identity, q = 0)
+ *   rec_node host [S][n_rec] receiver nodes per source (P_a: on-grid sampling);
+ *            must be distinct within a source; n_rec may be 0
+ *   out      receives the new tangent (owned by the library)
+ * Canonical order (the paper fixes none): component id = its smallest node; level =
+ * longest path in the condensation; components ordered by (level, smallest node),
+ * nodes ascending inside a component.  Synchronizes the stream (sizes are read back).
+ * Returns EIK_ERR_SINGULAR_BLOCK if a block pivot falls below lu_pivot_tol.
+ */
+int tangent_build(const eik_grid *g, const double *T, const double *s, int S,
+                  const int *src_node, const int *rec_node, int n_rec,
+                  const eik_opts *opts, eik_tangent **out, eik_stream stream);
+
+/*
+ * tangent_apply -- J p for all sources (Sec. 4.4, Eq. source-jacobian, D = 0;
+ * Alg. 1 steps 15-16): ds = M p, q = C ds, dT = A^-1 q by the forward block traversal
+ * B_a, d_rec = P dT.
+ *   p            device: [N][R] if shared_model else [S][N][R]
+ *   dT_full      device [S][N][R] or NULL (then an internal workspace holds dT)
+ *   d_rec        device [S][n_rec][R] or NULL
+ *   dtype        EIK_F64: FP64 vectors and arithmetic; EIK_F32: FP32 vectors, weights
+ *                and accumulation, FP64 SCC block solves.
+ * Asynchronous; device faults are latched (see tangent_status).
+ */
+int tangent_apply(eik_tangent *t, const void *p, int shared_model, int R,
+                  void *dT_full, void *d_rec, int dtype, eik_stream stream);
+
+/*
+ * tangent_apply_T -- J^T y (Sec. 4.4, Eq. source-transpose, D = 0; Alg. 1 steps
+ * 17-18): r = P^T y, lam = A^-T r by the reverse block traversal B_a^T (U^T, L^T, P^T
+ * on blocks), g_a = M^T C^T lam_a, and g = sum_a g_a when sum_sources.
+ *   y            device [S][n_rec][R]
+ *   g            device [N][R] if sum_sources else [S][N][R]
+ *   lam_full     device [S][N][R] or NULL (internal workspace)
+ * The source sum is a deterministic reduction in source order (FP64 accumulation for
+ * EIK_F32).
+ */
+int tangent_apply_T(eik_tangent *t, const void *y, int R, int sum_sources,
+                    void *g, void *lam_full, int dtype, eik_stream stream);
+
+/*
+ * tangent_solve / tangent_solve_T -- the bare transport solves dT = A^-1 q and
+ * lam = A^-T r for all sources (Prop. 3, Sec. 4.3), q and r device [S][N][R],
+ * outputs device [S][N][R].  Used for parity tests of the traversal alone.
+ */
+int tangent_solve(eik_tangent *t, const void *q, int R, void *x, int dtype, eik_stream stream);
+int tangent_solve_T(eik_tangent *t, const void *r, int R, void *x, int dtype, eik_stream stream);
+
+/* Counts of one source's structure (Sec. 5.2, Eq. graph-fractions; Table 4 rows). Host. */
+int tangent_stats(const eik_tangent *t, int source, eik_stats *out);
+
+/* Number of sources S, nodes N and receivers per source held by the tangent. */
+int tangent_dims(const eik_tangent *t, int *S, int64_t *N, int *n_rec);
+
+/*
+ * tangent_export -- one source's structure for bit-exact checks, into host buffers:
+ *   label     [N]  SCC id (smallest node of the component), or NULL
+ *   level     [N]  level of each node's component, or NULL
+ *   perm      [N]  canonical position -> node, or NULL
+ *   level_ptr [levels+1] first position of each level, or NULL
+ *   row_ptr   [N+1], col [edges], w [edges]  gather-form rows A = I - W in natural
+ *             node order (FP64 weights), each NULL-able
+ *   cs        [N]  calibration c^(s) (0 on the seed row), or NULL
+ * Synchronizes the device.
+ */
+int tangent_export(const eik_tangent *t, int source, int *label, int *level, int *perm,
+                   int64_t *level_ptr, int64_t *row_ptr, int *col, double *w, double *cs);
+
+/*
+ * tangent_status -- waits for the tangent's work on `stream` and returns the first
+ * device-side fault latched since the last call (EIK_ERR_TIMEOUT for a bounded wait
+ * that ran out), then clears it.
+ */
+int tangent_status(eik_tangent *t, eik_stream stream);
+
+/*
+ * tangent_debug_hold -- test hook for the bounded device-side waits of the persistent
+ * schedule.  Raises by one the number of completed items the forward traversal waits
+ * for before (source, step), so that wait can never be satisfied: the next persistent
+ * tangent_apply / tangent_solve ends after about wait_timeout_s and tangent_status
+ * returns EIK_ERR_TIMEOUT.  source < 0 undoes every hold.  No fault is raised on the
+ * device; the context stays usable.
+ */
+int tangent_debug_hold(eik_tangent *t, int source, int step);
+
+/* Release everything the tangent owns (waits for its streams). NULL is ignored. */
+void tangent_free(eik_tangent *t);
+
+/*
+ * sweep_apply -- the plain form: directional Gauss-Seidel sweeping (Sec. 3.6) of the
+ * same frozen A (or A^T when transpose != 0) over the 2^ndim logical orderings,
+ * hyperplane-parallel on the device, all sources and right-hand sides at once, cycled
+ * until max |dx| <= sweep_tol * max |x| over one full cycle.
+ *   b, x     device [S][N][R] (x is overwritten; starts from 0)
+ *   cycles   host, optional: cycles used
+ * Returns EIK_ERR_NOT_CONVERGED at sweep_max_cycles.  Synchronizes once per cycle.
+ */
+int sweep_apply(eik_tangent *t, int transpose, const void *b, int R, void *x, int dtype,
+                const eik_opts *opts, int *cycles, eik_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EIK_H */

@@ -73,6 +73,8 @@ def lib():
         L.or_sweep.restype = Lg
         L.or_kahn_residual.argtypes = [Lg, _pl, _pi, _pc]
         L.or_kahn_residual.restype = Lg
+        L.or_eik_lf.argtypes = [I, _pi, _pd, _pd, _pd, Lg, D, D, Lg, _pd]
+        L.or_eik_lf.restype = Lg
         _lib = L
     return _lib
 
@@ -303,6 +305,17 @@ def sweep(grid, t: Tangent, b: np.ndarray, transpose=False, tol=1e-12, max_cycle
         cyc = lib().or_sweep(grid.ndim, n, 0, t.row_ptr, t.col, t.w, np.ascontiguousarray(b, dtype=np.float64),
                              x, tol, max_cycles)
     return x, int(cyc)
+
+
+# --------------------------------------------------------------------------- state
+def eik_forward(grid, s, src, radius=1.0, tol=1e-12, max_cycles=2000):
+    """Sec. 2.1-2.2 (reading): factored full-metric Lax-Friedrichs sweeping for one source.
+    radius is in units of the largest logical spacing.  Returns (T [N], cycles)."""
+    n, dxi = _n(grid)
+    T = np.zeros(grid.N)
+    cyc = lib().or_eik_lf(grid.ndim, n, dxi, np.ascontiguousarray(grid.xyz), np.ascontiguousarray(s, dtype=np.float64),
+                          int(src), float(radius) * max(grid.dxi), float(tol), int(max_cycles), T)
+    return T, int(cyc)
 
 
 # --------------------------------------------------------------------------- maps and J

@@ -515,3 +515,104 @@ long or_kahn_residual(long N, const long *row_ptr, const int *col, char *removed
     free(indeg); free(optr); free(fill); free(succ); free(queue);
     return N - qt;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.1-2.2: first-arrival state of one point source.  The paper cites   */
+/* its factored topography-dependent solver without giving it; the oracle    */
+/* states one reading: the factored full-metric equation                     */
+/*   sqrt(P^T G P) = s,  P = tau g0 + T0 grad_xi tau,  T = T0 tau,            */
+/*   T0 = s_src |x - x_src|,  g0 = J^T grad_x T0,                             */
+/* solved by Lax-Friedrichs Gauss-Seidel sweeping (Kao, Osher, Qian 2004).    */
+/* For each of the 2^ndim orderings: every interior node not within `radius` */
+/* of the source (those keep tau = 1) is updated lexicographically with      */
+/* node-local viscosity alpha_d = T0 sqrt(G_dd):                              */
+/*   p_d = (tau+ - tau-)/(2 h_d),  P_b = tau g0_b + T0 p_b,                   */
+/*   H = sqrt(sum_a P_a sum_b G_ab P_b),                                      */
+/*   tau = ((s - H) + sum_d alpha_d (tau+ + tau-)/(2 h_d)) / sum_d alpha_d/h_d */
+/* then every boundary node takes the value of its nearest interior node     */
+/* along the inward diagonal (one step inward along each boundary axis);    */
+/* this keeps the iteration monotone.  Start tau = 1; stop when the largest  */
+/* change over one cycle is below tol.  Writes T [N]; returns cycles or -1.  */
+/* ------------------------------------------------------------------------ */
+long or_eik_lf(int ndim, const int *n, const double *dxi, const double *xyz, const double *s, long src,
+               double radius, double tol, long max_cycles, double *T)
+{
+    long st[3], N = 1;
+    int idx[3];
+    const int nd2 = ndim * ndim;
+    for (int d = 0; d < ndim; ++d) { N *= n[d]; if (n[d] < 3) return -2; }
+    strides(ndim, n, st);
+    double *Jm = malloc(N * nd2 * sizeof(double)), *G = malloc(N * nd2 * sizeof(double));
+    double *T0 = malloc(N * sizeof(double)), *g0 = malloc(N * ndim * sizeof(double));
+    double *alpha = malloc(N * ndim * sizeof(double)), *tau = malloc(N * sizeof(double));
+    char *fixed = malloc(N);
+    or_metric(ndim, n, dxi, xyz, Jm, G, NULL);
+    double ss = s[src];
+    for (long i = 0; i < N; ++i) {
+        double dd[3], r2 = 0.0;
+        for (int c = 0; c < ndim; ++c) { dd[c] = xyz[i * ndim + c] - xyz[src * ndim + c]; r2 = r2 + dd[c] * dd[c]; }
+        double r = sqrt(r2);
+        T0[i] = ss * r;
+        double gx[3];
+        for (int c = 0; c < ndim; ++c) gx[c] = r > 0.0 ? ss * dd[c] / r : 0.0;
+        for (int b = 0; b < ndim; ++b) {
+            double acc = 0.0;
+            for (int c = 0; c < ndim; ++c) acc = acc + Jm[i * nd2 + c * ndim + b] * gx[c];
+            g0[i * ndim + b] = acc;
+        }
+        for (int b = 0; b < ndim; ++b) alpha[i * ndim + b] = T0[i] * sqrt(G[i * nd2 + b * ndim + b]);
+        fixed[i] = r <= radius;
+        tau[i] = 1.0;
+    }
+    long used = -1;
+    int nord = 1 << ndim;
+    int lo2 = ndim == 3 ? 1 : 0, hi2 = ndim == 3 ? n[2] - 1 : 1, n2 = ndim == 3 ? n[2] : 1;
+    for (long cyc = 1; cyc <= max_cycles && used < 0; ++cyc) {
+        double dmax = 0.0;
+        for (int o = 0; o < nord; ++o) {
+            for (int c0 = 1; c0 < n[0] - 1; ++c0)
+                for (int c1 = 1; c1 < n[1] - 1; ++c1)
+                    for (int c2 = lo2; c2 < hi2; ++c2) {
+                        idx[0] = (o & 1) ? n[0] - 1 - c0 : c0;
+                        idx[1] = (o & 2) ? n[1] - 1 - c1 : c1;
+                        idx[2] = ndim == 3 ? ((o & 4) ? n2 - 1 - c2 : c2) : 0;
+                        long i = ndim == 3 ? ((long)idx[0] * n[1] + idx[1]) * n2 + idx[2] : (long)idx[0] * n[1] + idx[1];
+                        if (fixed[i]) continue;
+                        double p[3], P[3];
+                        for (int d = 0; d < ndim; ++d) p[d] = (tau[i + st[d]] - tau[i - st[d]]) / (2.0 * dxi[d]);
+                        for (int b = 0; b < ndim; ++b) P[b] = tau[i] * g0[i * ndim + b] + T0[i] * p[b];
+                        double H2 = 0.0;
+                        for (int x = 0; x < ndim; ++x) {
+                            double row = 0.0;
+                            for (int b = 0; b < ndim; ++b) row = row + G[i * nd2 + x * ndim + b] * P[b];
+                            H2 = H2 + P[x] * row;
+                        }
+                        double num = s[i] - sqrt(H2), den = 0.0;
+                        for (int d = 0; d < ndim; ++d) {
+                            num = num + alpha[i * ndim + d] * (tau[i + st[d]] + tau[i - st[d]]) / (2.0 * dxi[d]);
+                            den = den + alpha[i * ndim + d] / dxi[d];
+                        }
+                        double nv = num / den;
+                        if (fabs(nv - tau[i]) > dmax) dmax = fabs(nv - tau[i]);
+                        tau[i] = nv;
+                    }
+            for (long i = 0; i < N; ++i) {
+                if (fixed[i]) continue;
+                coords(ndim, n, i, idx);
+                long step = 0;
+                for (int d = 0; d < ndim; ++d) {
+                    if (idx[d] == 0) step += st[d];
+                    else if (idx[d] == n[d] - 1) step -= st[d];
+                }
+                if (step == 0) continue;
+                double nv = tau[i + step];
+                if (fabs(nv - tau[i]) > dmax) dmax = fabs(nv - tau[i]);
+                tau[i] = nv;
+            }
+        }
+        if (dmax < tol) used = cyc;
+    }
+    for (long i = 0; i < N; ++i) T[i] = T0[i] * tau[i];
+    free(Jm); free(G); free(T0); free(g0); free(alpha); free(tau); free(fixed);
+    return used;
+}

@@ -1,0 +1,249 @@
+// First-arrival state T = T0 tau for point sources (Sec. 2.1-2.2): the paper takes its
+// nonlinear state from a cited factored topography-dependent solver without giving the
+// scheme; this file solves the factored full-metric equation
+//     H(tau, grad_xi tau) = sqrt(P^T G P) = s,   P = tau g0 + T0 grad_xi tau,
+// with T0 = s_src |x - x_src|, g0 = J^T grad_x T0, by first-order Lax-Friedrichs
+// sweeping (Kao, Osher and Qian, 2004): Gauss-Seidel over the 2^ndim logical orderings,
+// each ordering run hyperplane by hyperplane (identical to the lexicographic sweep).
+// Node update (interior, tau_+/- the neighbours along axis d, h_d the spacing):
+//     p_d   = (tau_+ - tau_-) / (2 h_d),   P_b = tau_i g0_b + T0 p_b,
+//     H     = sqrt(sum_a P_a (sum_b G_ab P_b)),   alpha_d = T0 sqrt(G_dd),
+//     tau_i = ((s_i - H) + sum_d alpha_d (tau_+ + tau_-) / (2 h_d)) / (sum_d alpha_d / h_d).
+// After every ordering each boundary node takes the value of its nearest interior node
+// along the inward diagonal (one step inward along every boundary axis), which keeps
+// the iteration monotone.  Nodes within eik_src_radius * max(h) of the source keep
+// tau = 1.  Start: tau = 1.  Stop: the largest |change| over one full cycle is below
+// eik_tol.
+// Compiled with -fmad=false so that every step is a separately rounded IEEE operation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "eik_internal.h"
+
+namespace eik {
+
+__global__ void k_metric(GridDesc g, const double *__restrict__ xyz, double *__restrict__ G, double *__restrict__ Jout);
+
+// per (source, node): T0, g0 = J^T grad_x T0, alpha_d, fixed flag
+__global__ void k_eik_prep(GridDesc g, int S, const double *__restrict__ xyz, const double *__restrict__ Jm,
+                           const double *__restrict__ G, const double *__restrict__ s, const int *__restrict__ src,
+                           double radius, double *T0, double *g0, double *alpha, unsigned char *fixed, double *tau)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= g.N * S) return;
+    const int nd = g.ndim;
+    long long a = v / g.N, i = v - a * g.N;
+    long long k = src[a];
+    double ss = s[k];
+    double d[3], r2 = 0.0;
+    for (int c = 0; c < nd; ++c) { d[c] = xyz[i * nd + c] - xyz[k * nd + c]; r2 = r2 + d[c] * d[c]; }
+    double r = sqrt(r2);
+    T0[v] = ss * r;
+    double gx[3];
+    for (int c = 0; c < nd; ++c) gx[c] = r > 0.0 ? ss * d[c] / r : 0.0;
+    for (int b = 0; b < nd; ++b) {
+        double acc = 0.0;
+        for (int c = 0; c < nd; ++c) acc = acc + Jm[i * nd * nd + c * nd + b] * gx[c];
+        g0[v * nd + b] = acc;
+    }
+    for (int b = 0; b < nd; ++b) alpha[v * nd + b] = T0[v] * sqrt(G[i * nd * nd + b * nd + b]);
+    fixed[v] = r <= radius ? 1 : 0;
+    tau[v] = 1.0;
+}
+
+struct LFParams {
+    GridDesc g;
+    int S, order, h, lo0, hi0;
+    const double *G, *s, *T0, *g0, *alpha;
+    const unsigned char *fixed;
+    double *tau;
+    unsigned long long *dmax;   // bit pattern of max |d tau| (non-negative double)
+};
+
+__device__ __forceinline__ double lf_update(const LFParams &P, long long a, long long i, const int *c)
+{
+    const GridDesc &g = P.g;
+    const int nd = g.ndim;
+    const long long v = a * g.N + i;
+    const double *tau = P.tau + a * g.N;
+    const double T0 = P.T0[v];
+    const double ti = tau[i];
+    double p[3], Pv[3];
+    for (int d = 0; d < nd; ++d) p[d] = (tau[i + g.st[d]] - tau[i - g.st[d]]) / (2.0 * g.dxi[d]);
+    for (int b = 0; b < nd; ++b) Pv[b] = ti * P.g0[v * nd + b] + T0 * p[b];
+    double H2 = 0.0;
+    for (int x = 0; x < nd; ++x) {
+        double row = 0.0;
+        for (int b = 0; b < nd; ++b) row = row + P.G[i * nd * nd + x * nd + b] * Pv[b];
+        H2 = H2 + Pv[x] * row;
+    }
+    double H = sqrt(H2);
+    double num = P.s[i] - H, den = 0.0;
+    for (int d = 0; d < nd; ++d) {
+        double al = P.alpha[v * nd + d];
+        num = num + al * (tau[i + g.st[d]] + tau[i - g.st[d]]) / (2.0 * g.dxi[d]);
+        den = den + al / g.dxi[d];
+    }
+    (void)c;
+    return num / den;
+}
+
+__global__ void k_lf_plane(LFParams P)
+{
+    const GridDesc &g = P.g;
+    const int nd = g.ndim;
+    // interior nodes only: coordinates 1..n-2 along every axis
+    const int m0 = g.n[0] - 2, m1 = g.n[1] - 2, m2 = nd == 3 ? g.n[2] - 2 : 1;
+    long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long span = (long long)(P.hi0 - P.lo0 + 1) * (nd == 3 ? m1 : 1);
+    if (tid >= span * P.S) return;
+    long long a = tid / span, cell = tid - a * span;
+    int c0, c1, c2;
+    if (nd == 3) {
+        c0 = P.lo0 + (int)(cell / m1);
+        c1 = (int)(cell % m1);
+        c2 = P.h - c0 - c1;
+        if (c2 < 0 || c2 >= m2) return;
+    } else {
+        c0 = P.lo0 + (int)cell;
+        c1 = P.h - c0;
+        c2 = 0;
+        if (c1 < 0 || c1 >= m1) return;
+    }
+    int i0 = 1 + ((P.order & 1) ? m0 - 1 - c0 : c0);
+    int i1 = 1 + ((P.order & 2) ? m1 - 1 - c1 : c1);
+    int i2 = nd == 3 ? 1 + ((P.order & 4) ? m2 - 1 - c2 : c2) : 0;
+    long long i = nd == 3 ? ((long long)i0 * g.n[1] + i1) * g.n[2] + i2 : (long long)i0 * g.n[1] + i1;
+    long long v = a * g.N + i;
+    if (P.fixed[v]) return;
+    int c[3] = {i0, i1, i2};
+    double nv = lf_update(P, a, i, c);
+    double old = P.tau[v];
+    P.tau[v] = nv;
+    double dd = fabs(nv - old);
+    atomicMax(P.dmax, (unsigned long long)__double_as_longlong(dd));
+}
+
+// boundary nodes take the value of the nearest interior node along the inward diagonal
+__global__ void k_lf_boundary(GridDesc g, int S, const unsigned char *__restrict__ fixed, double *tau,
+                              unsigned long long *dmax)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= g.N * S || fixed[v]) return;
+    long long a = v / g.N, i = v - a * g.N;
+    int c[3];
+    if (g.ndim == 3) { c[2] = (int)(i % g.n[2]); c[1] = (int)((i / g.n[2]) % g.n[1]); c[0] = (int)(i / g.st[0]); }
+    else { c[1] = (int)(i % g.n[1]); c[0] = (int)(i / g.n[1]); c[2] = 0; }
+    long long step = 0;
+    for (int d = 0; d < g.ndim; ++d) {
+        if (c[d] == 0) step += g.st[d];
+        else if (c[d] == g.n[d] - 1) step -= g.st[d];
+    }
+    if (step == 0) return;
+    double *ta = tau + a * g.N;
+    double nv = ta[i + step];
+    double dd = fabs(nv - ta[i]);
+    ta[i] = nv;
+    atomicMax(dmax, (unsigned long long)__double_as_longlong(dd));
+}
+
+__global__ void k_eik_out(long long SN, const double *T0, const double *tau, double *T)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v < SN) T[v] = T0[v] * tau[v];
+}
+
+}  // namespace eik
+
+using namespace eik;
+
+extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const int *src_node, double *T,
+                           const eik_opts *opts_in, int *cycles, eik_stream stream)
+{
+    try {
+        if (!gin || (gin->ndim != 2 && gin->ndim != 3) || !gin->xyz || !s || !T || !src_node || S <= 0) {
+            set_error("bad eik_forward arguments");
+            return EIK_ERR_INVALID;
+        }
+        eik_opts def;
+        eik_opts_default(&def);
+        const eik_opts *opts = opts_in ? opts_in : &def;
+        GridDesc g = make_grid_desc(gin);
+        for (int d = 0; d < g.ndim; ++d)
+            if (g.n[d] < 3) { set_error("grid needs >= 3 nodes per axis"); return EIK_ERR_INVALID; }
+        for (int a = 0; a < S; ++a)
+            if (src_node[a] < 0 || src_node[a] >= g.N) { set_error("source node out of range"); return EIK_ERR_INVALID; }
+        cudaStream_t st = (cudaStream_t)stream;
+        const int nd = g.ndim;
+        const long long N = g.N, SN = N * S;
+        double *G = nullptr, *Jm = nullptr, *T0 = nullptr, *g0 = nullptr, *alpha = nullptr, *tau = nullptr;
+        unsigned char *fixed = nullptr;
+        int *src_d = nullptr;
+        unsigned long long *dmax = nullptr;
+        auto release = [&]() {
+            cudaFree(G); cudaFree(Jm); cudaFree(T0); cudaFree(g0); cudaFree(alpha); cudaFree(tau);
+            cudaFree(fixed); cudaFree(src_d); cudaFree(dmax);
+        };
+#define TRY(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { int rc_ = cuda_fail(e_, #call, __FILE__, __LINE__); release(); return rc_; } } while (0)
+        TRY(cudaMalloc(&G, N * nd * nd * sizeof(double)));
+        TRY(cudaMalloc(&Jm, N * nd * nd * sizeof(double)));
+        TRY(cudaMalloc(&T0, SN * sizeof(double)));
+        TRY(cudaMalloc(&g0, SN * nd * sizeof(double)));
+        TRY(cudaMalloc(&alpha, SN * nd * sizeof(double)));
+        TRY(cudaMalloc(&tau, SN * sizeof(double)));
+        TRY(cudaMalloc(&fixed, SN));
+        TRY(cudaMalloc(&src_d, S * sizeof(int)));
+        TRY(cudaMalloc(&dmax, sizeof(unsigned long long)));
+        TRY(cudaMemcpyAsync(src_d, src_node, S * sizeof(int), cudaMemcpyHostToDevice, st));
+        double hmax = 0.0;
+        for (int d = 0; d < nd; ++d) hmax = std::max(hmax, g.dxi[d]);
+        k_metric<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(g, gin->xyz, G, Jm);
+        k_eik_prep<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(g, S, gin->xyz, Jm, G, s, src_d,
+                                                                  opts->eik_src_radius * hmax, T0, g0, alpha, fixed, tau);
+        TRY(cudaGetLastError());
+        LFParams P{};
+        P.g = g; P.S = S; P.G = G; P.s = s; P.T0 = T0; P.g0 = g0; P.alpha = alpha; P.fixed = fixed; P.tau = tau;
+        P.dmax = dmax;
+        const int m0 = g.n[0] - 2, m1 = g.n[1] - 2, m2 = nd == 3 ? g.n[2] - 2 : 1;
+        const int hmax_i = (m0 - 1) + (m1 - 1) + (nd == 3 ? m2 - 1 : 0);
+        const int nord = 1 << nd;
+        int used = -1;
+        for (int cyc = 1; cyc <= opts->eik_max_cycles; ++cyc) {
+            TRY(cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), st));
+            for (int o = 0; o < nord; ++o) {
+                P.order = o;
+                for (int h = 0; h <= hmax_i; ++h) {
+                    P.h = h;
+                    int rest = hmax_i - (m0 - 1);
+                    P.lo0 = std::max(0, h - rest);
+                    P.hi0 = std::min(m0 - 1, h);
+                    long long span = (long long)(P.hi0 - P.lo0 + 1) * (nd == 3 ? m1 : 1) * S;
+                    k_lf_plane<<<(unsigned)((span + 255) / 256), 256, 0, st>>>(P);
+                }
+                k_lf_boundary<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(g, S, fixed, tau, dmax);
+            }
+            TRY(cudaGetLastError());
+            unsigned long long hb = 0;
+            TRY(cudaMemcpyAsync(&hb, dmax, sizeof hb, cudaMemcpyDeviceToHost, st));
+            TRY(cudaStreamSynchronize(st));
+            double dm;
+            std::memcpy(&dm, &hb, sizeof dm);
+            if (dm < opts->eik_tol) { used = cyc; break; }
+        }
+        k_eik_out<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(SN, T0, tau, T);
+        TRY(cudaGetLastError());
+        TRY(cudaStreamSynchronize(st));
+#undef TRY
+        release();
+        if (cycles) *cycles = used < 0 ? opts->eik_max_cycles : used;
+        if (used < 0) { set_error("eik_forward did not converge in %d cycles", opts->eik_max_cycles); return EIK_ERR_NOT_CONVERGED; }
+        return EIK_OK;
+    } catch (...) {
+        set_error("eik_forward failed");
+        return EIK_ERR_INVALID;
+    }
+}

@@ -1,0 +1,133 @@
+// Internal declarations shared by the libeik translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "eik.h"
+
+namespace eik {
+
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define EIK_CHECK(call)                                                        \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) return eik::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define EIK_CHECK_LAUNCH() EIK_CHECK(cudaGetLastError())
+
+// Device-side fault codes latched in Tangent::err (first one wins).
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_SINGULAR = 2, DEV_BAD_INDEX = 3 };
+
+struct GridDesc {
+    int ndim;
+    int n[3];
+    double dxi[3];
+    long long N;
+    long long st[3];   // strides of the logical dimensions in the linear index
+};
+
+GridDesc make_grid_desc(const eik_grid *g);
+
+// A nontrivial SCC block of one source.
+struct Block {
+    int src;        // source
+    int p0;         // first position (canonical order) of the block
+    int k;          // size
+    int level;      // level of the block in the condensation
+    long long lu;   // offset of the k*k FP64 factors
+    long long piv;  // offset of the k pivots
+    long long ws;   // offset (in rows) of the block's rows in the workspace
+};
+
+struct Tangent {
+    int S = 0;
+    long long N = 0;
+    int n_rec = 0;
+    int model = 0;
+    int maxL = 0;
+    GridDesc grid{};
+    eik_opts opts{};
+    int device = 0;
+    int num_sms = 0;
+
+    std::vector<int> nlev;                 // [S]
+    std::vector<long long> level_ptr;      // [S][maxL+1] host copy
+    std::vector<long long> ebase;          // [S+1] forward edge base
+    std::vector<long long> tbase;          // [S+1] transposed edge base
+    long long *ebase_d = nullptr;          // device copies of ebase / tbase
+    long long *tbase_d = nullptr;
+    std::vector<Block> blocks;
+    std::vector<eik_stats> stats;          // [S]
+
+    // ---- device structure, canonical (level-permuted) order unless noted
+    int *perm = nullptr;      // [S][N] node at position; ~node (<0) for block members
+    int *pos = nullptr;       // [S][N] natural -> position
+    int *label = nullptr;     // [S][N] natural: SCC id (smallest local node)
+    int *level = nullptr;     // [S][N] natural: level of the node's component
+    int *rowptr = nullptr;    // [S][N+1] local offsets into the forward edge arrays
+    int *up_node = nullptr;   // [E] upstream node j (natural index)
+    float *up_w32 = nullptr;
+    double *up_w64 = nullptr;
+    int *cptr = nullptr;      // [S][N+1] local offsets into the transposed edge arrays
+    int *dn_node = nullptr;   // [E'] downstream node i (natural index)
+    float *dn_w32 = nullptr;
+    double *dn_w64 = nullptr;
+    double *cq64 = nullptr;   // [S][N] C*M coefficient per position
+    float *cq32 = nullptr;
+    double *cqn64 = nullptr;  // [S][N] same, natural order (source-sum reduction)
+    float *cqn32 = nullptr;
+    int *rec_slot = nullptr;  // [S][N] receiver index per position, -1 if none
+    int *rec_nat = nullptr;   // [S][n_rec] receiver nodes
+    // natural-order rows for export
+    int *nrow_cnt = nullptr;      // [S][N]
+    int *nrow_node = nullptr;     // [S][N][2*ndim]
+    double *nrow_w = nullptr;     // [S][N][2*ndim]
+    double *cs_nat = nullptr;     // [S][N]
+    // blocks
+    int nblk = 0;
+    int4 *blk_desc = nullptr;     // {src, p0, k, level}
+    long long *blk_off = nullptr; // [nblk][3] {lu, piv, ws}
+    double *lu = nullptr;
+    int *piv = nullptr;
+    long long lu_words = 0, piv_words = 0, ws_rows = 0;
+    // work items of the traversals: {src, step, p0, p1} or {src, step, ~blk, 0}
+    int nitems = 0;
+    int4 *items_fwd = nullptr;
+    int4 *items_bwd = nullptr;
+    std::vector<int> step_ptr_fwd, step_ptr_bwd;   // [maxL+1] items per step (host)
+    int *item_cnt = nullptr;      // [S][maxL] items per (source, level); bwd uses reversed step
+    int *done = nullptr;          // [S][maxL] completed items per (source, step)
+    int *ticket = nullptr;        // [2]
+    int *err = nullptr;           // [4] device fault latch {code, source, step, item}
+    // workspaces
+    void *ws_vec = nullptr;       // internal dT / lam
+    size_t ws_vec_bytes = 0;
+    double *ws_blk = nullptr;     // block right-hand sides
+    size_t ws_blk_elems = 0;
+    int host_err = 0;
+    std::vector<long long> holds;   // item_cnt entries raised by tangent_debug_hold
+};
+
+int build_tangent(const eik_grid *g, const double *T, const double *s, int S, const int *src_node,
+                  const int *rec_node, int n_rec, const eik_opts *opts, Tangent **out,
+                  cudaStream_t stream);
+void free_tangent(Tangent *t);
+
+enum Mode : int { MODE_J = 0, MODE_RAW = 1 };
+
+int traverse(Tangent *t, bool transpose, int mode, const void *in, int shared_in, int R,
+             void *out_full, void *out_aux, int sum_sources, int dtype, cudaStream_t stream);
+
+int sweep(Tangent *t, bool transpose, const void *b, int R, void *x, int dtype,
+          const eik_opts *opts, int *cycles, cudaStream_t stream);
+
+int ensure_workspace(Tangent *t, size_t vec_bytes, size_t blk_elems);
+
+}  // namespace eik

@@ -1,0 +1,1152 @@
+// Phase I of Algorithm 1 on the device: metric, face-upwind rows and calibration,
+// dependency graph, SCC condensation with canonical levels, block LU, traversal items.
+//
+// This translation unit is compiled with -fmad=false: the sign of every face
+// coefficient a_f decides whether an edge exists, and it must come out of the same
+// sequence of correctly rounded IEEE operations that the formulas below state.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "eik_internal.h"
+
+namespace eik {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+const char *last_error() { return g_err.c_str(); }
+
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line)
+{
+    set_error("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    return e == cudaErrorMemoryAllocation ? EIK_ERR_OOM : EIK_ERR_CUDA;
+}
+
+GridDesc make_grid_desc(const eik_grid *g)
+{
+    GridDesc d{};
+    d.ndim = g->ndim;
+    d.N = 1;
+    for (int a = 0; a < 3; ++a) { d.n[a] = a < g->ndim ? g->n[a] : 1; d.dxi[a] = a < g->ndim ? g->dxi[a] : 1.0; }
+    for (int a = 0; a < g->ndim; ++a) d.N *= g->n[a];
+    if (g->ndim == 3) { d.st[2] = 1; d.st[1] = g->n[2]; d.st[0] = (long long)g->n[1] * g->n[2]; }
+    else { d.st[1] = 1; d.st[0] = g->n[1]; d.st[2] = 0; }
+    return d;
+}
+
+constexpr int INF = 0x7fffffff;
+
+__device__ __forceinline__ void node_coords(const GridDesc &g, long long i, int *c)
+{
+    if (g.ndim == 3) { c[2] = (int)(i % g.n[2]); c[1] = (int)((i / g.n[2]) % g.n[1]); c[0] = (int)(i / g.st[0]); }
+    else { c[1] = (int)(i % g.n[1]); c[0] = (int)(i / g.n[1]); c[2] = 0; }
+}
+
+// derivative along logical axis `ax` of component `comp` of an interleaved field:
+// central difference inside, second-order one-sided difference on the two edges
+__device__ double axis_derivative(const double *f, int ncomp, int comp, long long i, int at, int nax,
+                                  long long step, double h)
+{
+    double num;
+    if (at == 0) {
+        num = (-3.0 * f[i * ncomp + comp] + 4.0 * f[(i + step) * ncomp + comp]) - f[(i + 2 * step) * ncomp + comp];
+    } else if (at == nax - 1) {
+        num = (3.0 * f[i * ncomp + comp] - 4.0 * f[(i - step) * ncomp + comp]) + f[(i - 2 * step) * ncomp + comp];
+    } else {
+        num = f[(i + step) * ncomp + comp] - f[(i - step) * ncomp + comp];
+    }
+    return num / (2.0 * h);
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 2.2, Eq. (metric-eikonal): Jm = dx/dxi (finite differences of the node
+// coordinates), Kinv = Jm^-1 by the adjugate, G = Kinv Kinv^T.
+// ---------------------------------------------------------------------------
+__global__ void k_metric(GridDesc g, const double *__restrict__ xyz, double *__restrict__ G,
+                         double *__restrict__ Jout)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    int c[3];
+    node_coords(g, i, c);
+    const int nd = g.ndim;
+    double Jm[3][3];
+    for (int a = 0; a < nd; ++a)
+        for (int b = 0; b < nd; ++b) Jm[a][b] = axis_derivative(xyz, nd, a, i, c[b], g.n[b], g.st[b], g.dxi[b]);
+    if (nd == 3) {
+        double m00 = Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1];
+        double m01 = Jm[1][2] * Jm[2][0] - Jm[1][0] * Jm[2][2];
+        double m02 = Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0];
+        double m10 = Jm[0][2] * Jm[2][1] - Jm[0][1] * Jm[2][2];
+        double m11 = Jm[0][0] * Jm[2][2] - Jm[0][2] * Jm[2][0];
+        double m12 = Jm[0][1] * Jm[2][0] - Jm[0][0] * Jm[2][1];
+        double m20 = Jm[0][1] * Jm[1][2] - Jm[0][2] * Jm[1][1];
+        double m21 = Jm[0][2] * Jm[1][0] - Jm[0][0] * Jm[1][2];
+        double m22 = Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0];
+        double det = (Jm[0][0] * m00 + Jm[0][1] * m01) + Jm[0][2] * m02;
+        double K[3][3] = {{m00 / det, m10 / det, m20 / det},
+                          {m01 / det, m11 / det, m21 / det},
+                          {m02 / det, m12 / det, m22 / det}};
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                G[i * 9 + a * 3 + b] = (K[a][0] * K[b][0] + K[a][1] * K[b][1]) + K[a][2] * K[b][2];
+    } else {
+        double det = Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0];
+        double K[2][2] = {{Jm[1][1] / det, -Jm[0][1] / det}, {-Jm[1][0] / det, Jm[0][0] / det}};
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) G[i * 4 + a * 2 + b] = K[a][0] * K[b][0] + K[a][1] * K[b][1];
+    }
+    if (Jout)
+        for (int a = 0; a < nd; ++a)
+            for (int b = 0; b < nd; ++b) Jout[i * nd * nd + a * nd + b] = Jm[a][b];
+}
+
+// nodal logical gradient of T for every source: gT [S][N][ndim]
+__global__ void k_grad(GridDesc g, int S, const double *__restrict__ T, double *__restrict__ gT)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= g.N * S) return;
+    long long a = v / g.N, i = v - a * g.N;
+    int c[3];
+    node_coords(g, i, c);
+    const double *Ta = T + a * g.N;
+    for (int b = 0; b < g.ndim; ++b)
+        gT[v * g.ndim + b] = axis_derivative(Ta, 1, 0, i, c[b], g.n[b], g.st[b], g.dxi[b]);
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 3.1-3.2: face-based upwind rows and calibration, one thread per (source, node).
+// Faces are visited axis ascending, lower side first.  For neighbour j across a face
+// normal to axis d: the face metric row and gradient are the averages of the two
+// nodes, except the normal gradient component, which is the compact difference across
+// the face; a_f = sum_b Gf[d][b] gf[b]; j is upstream iff -side * a_f > 0, with
+// coupling c = -side * a_f / h_d.  Row: d_i = sum c, w = c / d_i; l_i = T_i - sum w T_j,
+// cs_i = l_i / s_i.  Seed rows (the source node) are identities with cs = 0; a non-seed
+// row without an upstream face is an identity with cs = T_i / s_i.
+// upmask bit (2 d + (side > 0)) marks an upstream face.
+// ---------------------------------------------------------------------------
+__global__ void k_assemble(GridDesc g, int S, const double *__restrict__ G, const double *__restrict__ gT,
+                           const double *__restrict__ T, const double *__restrict__ s, const int *__restrict__ src,
+                           int *__restrict__ cnt, int *__restrict__ nnode, double *__restrict__ nw,
+                           unsigned char *__restrict__ upmask, double *__restrict__ cs,
+                           unsigned long long *__restrict__ n_identity)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= g.N * S) return;
+    const int nd = g.ndim, nd2 = nd * nd, slots = 2 * nd;
+    long long a = v / g.N, i = v - a * g.N;
+    const double *Ta = T + a * g.N;
+    const double *gTa = gT + a * g.N * nd;
+    if (i == src[a]) {
+        cnt[v] = 0; upmask[v] = 0; cs[v] = 0.0;
+        return;
+    }
+    int c[3];
+    node_coords(g, i, c);
+    int m = 0;
+    unsigned char mask = 0;
+    double cw[6];
+    int nb[6];
+    for (int d = 0; d < nd; ++d) {
+        for (int side = -1; side <= 1; side += 2) {
+            int at = c[d] + side;
+            if (at < 0 || at >= g.n[d]) continue;
+            long long j = i + side * g.st[d];
+            double gf[3];
+            for (int b = 0; b < nd; ++b) gf[b] = (gTa[i * nd + b] + gTa[j * nd + b]) * 0.5;
+            gf[d] = side < 0 ? (Ta[i] - Ta[j]) / g.dxi[d] : (Ta[j] - Ta[i]) / g.dxi[d];
+            double af = 0.0;
+            for (int b = 0; b < nd; ++b) {
+                double Gf = (G[i * nd2 + d * nd + b] + G[j * nd2 + d * nd + b]) * 0.5;
+                af = af + Gf * gf[b];
+            }
+            double up = side < 0 ? af : -af;
+            if (up > 0.0) {
+                nb[m] = (int)j;
+                cw[m] = up / g.dxi[d];
+                mask |= (unsigned char)(1u << (2 * d + (side > 0)));
+                ++m;
+            }
+        }
+    }
+    cnt[v] = m;
+    upmask[v] = mask;
+    if (m == 0) {
+        cs[v] = Ta[i] / s[i];
+        atomicAdd(n_identity + a, 1ull);
+        return;
+    }
+    double dsum = 0.0;
+    for (int e = 0; e < m; ++e) dsum = dsum + cw[e];
+    double acc = 0.0;
+    for (int e = 0; e < m; ++e) {
+        double w = cw[e] / dsum;
+        nnode[v * slots + e] = nb[e];
+        nw[v * slots + e] = w;
+        acc = acc + w * Ta[nb[e]];
+    }
+    cs[v] = (Ta[i] - acc) / s[i];
+}
+
+// ---------------------------------------------------------------------------
+// Dependency graph helpers.  Global vertex id v = source * N + node; an edge u -> v
+// exists iff bit (2 d + (side > 0)) of upmask[v] is set with u = v + side * st[d].
+// ---------------------------------------------------------------------------
+template <typename F>
+__device__ __forceinline__ void for_preds(const GridDesc &g, long long v, unsigned char mask, F f)
+{
+    for (int b = 0; b < 2 * g.ndim; ++b)
+        if (mask & (1u << b)) {
+            int d = b >> 1, side = (b & 1) ? 1 : -1;
+            f(v + side * g.st[d]);
+        }
+}
+
+// successors u of v: neighbours whose upstream face points back at v
+template <typename F>
+__device__ __forceinline__ void for_succs(const GridDesc &g, long long v, const unsigned char *upmask, F f)
+{
+    int c[3];
+    node_coords(g, v % g.N, c);
+    for (int d = 0; d < g.ndim; ++d)
+        for (int side = -1; side <= 1; side += 2) {
+            int at = c[d] + side;
+            if (at < 0 || at >= g.n[d]) continue;
+            long long u = v + side * g.st[d];
+            if (upmask[u] & (1u << (2 * d + (side < 0)))) f(u);
+        }
+}
+
+// Kahn rounds (Sec. 3.5): fst[v] = first round in which every predecessor of v was
+// already removed.  A predecessor stamped in the current round does not count, so the
+// result does not depend on thread order.
+__global__ void k_fwd_trim(GridDesc g, long long SN, const unsigned char *__restrict__ upmask, int *fst, int t,
+                           int *changed)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= SN || fst[v] != INF) return;
+    bool ready = true;
+    for_preds(g, v, upmask[v], [&](long long u) { if (fst[u] >= t) ready = false; });
+    if (ready) { fst[v] = t; *changed = 1; }
+}
+
+// backward trimming of the Kahn residual: remove vertices none of whose successors
+// inside the residual remains
+__global__ void k_bwd_trim(GridDesc g, long long SN, const unsigned char *__restrict__ upmask,
+                           const int *__restrict__ fst, int *bst, int t, int *changed)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= SN || fst[v] != INF || bst[v] != INF) return;
+    bool ready = true;
+    for_succs(g, v, upmask, [&](long long u) { if (fst[u] == INF && bst[u] >= t) ready = false; });
+    if (ready) { bst[v] = t; *changed = 1; }
+}
+
+__global__ void k_collect(long long SN, const int *__restrict__ fst, const int *__restrict__ bst, int *list, int *count,
+                          int *label, int *act)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= SN) return;
+    if (fst[v] == INF && bst[v] == INF) {
+        int k = atomicAdd(count, 1);
+        list[k] = (int)v;
+        act[v] = 1;
+        label[v] = -1;
+    } else {
+        act[v] = 0;
+        label[v] = (int)v;
+    }
+}
+
+// Colouring SCC (forward min-label propagation + backward closure from the roots):
+// colour[v] = smallest active vertex that reaches v; the vertices with the root's
+// colour that reach the root form the root's SCC, whose smallest vertex is the root.
+__global__ void k_color_init(const int *list, int n, const int *act, int *color, int *inscc)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int v = list[k];
+    if (!act[v]) return;
+    color[v] = v;
+    inscc[v] = 0;
+}
+
+__global__ void k_color_prop(GridDesc g, const int *list, int n, const unsigned char *__restrict__ upmask,
+                             const int *act, int *color, int *changed)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int v = list[k];
+    if (!act[v]) return;
+    int m = color[v];
+    for_preds(g, v, upmask[v], [&](long long u) {
+        if (act[u]) { int cu = *(volatile int *)&color[u]; if (cu < m) m = cu; }
+    });
+    if (m < color[v]) { atomicMin(&color[v], m); *changed = 1; }
+}
+
+__global__ void k_scc_roots(const int *list, int n, const int *act, const int *color, int *inscc)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int v = list[k];
+    if (act[v] && color[v] == v) inscc[v] = 1;
+}
+
+__global__ void k_scc_back(GridDesc g, const int *list, int n, const unsigned char *__restrict__ upmask, const int *act,
+                           const int *color, int *inscc, int *changed)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int v = list[k];
+    if (!act[v] || inscc[v]) return;
+    bool hit = false;
+    int cv = color[v];
+    for_succs(g, v, upmask, [&](long long u) {
+        if (act[u] && color[u] == cv && *(volatile int *)&inscc[u]) hit = true;
+    });
+    if (hit) { inscc[v] = 1; *changed = 1; }
+}
+
+__global__ void k_scc_take(const int *list, int n, int *act, const int *color, const int *inscc, int *label,
+                           int *remaining)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int v = list[k];
+    if (!act[v]) return;
+    if (inscc[v]) { label[v] = color[v]; act[v] = 0; }
+    else atomicAdd(remaining, 1);
+}
+
+__global__ void k_comp_size(long long SN, const int *__restrict__ label, int *csize)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= SN) return;
+    atomicAdd(&csize[label[v]], 1);
+}
+
+// ---------------------------------------------------------------------------
+// Canonical levels (longest path in the condensation DAG), in rounds: a component is
+// assigned in round t once all of its external predecessor components were assigned
+// in earlier rounds; its level is 1 + the largest of theirs (0 without predecessor).
+// The per-component values live at the component's root vertex.
+// ---------------------------------------------------------------------------
+__global__ void k_lvl_init(long long SN, const int *__restrict__ fst, const int *__restrict__ label, int *lvl, int *asg,
+                           int *cmax, int *blk, int *list, int *count)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= SN) return;
+    // vertices removed by forward Kahn are singletons with all ancestors removed too:
+    // their Kahn round is their longest-path level
+    if (fst[v] != INF) { lvl[v] = fst[v]; asg[v] = -1; }
+    else {
+        if (label[v] == v) { asg[v] = INF; cmax[v] = -1; blk[v] = -1; }
+        int k = atomicAdd(count, 1);
+        list[k] = (int)v;
+    }
+}
+
+__global__ void k_lvl_scan(GridDesc g, const int *list, int n, const unsigned char *__restrict__ upmask,
+                           const int *__restrict__ label, const int *lvl, const int *asg, int *cmax, int *blk, int t)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int v = list[k];
+    int c = label[v];
+    if (asg[c] != INF) return;
+    int m = -1;
+    bool blocked = false;
+    for_preds(g, v, upmask[v], [&](long long u) {
+        int cu = label[u];
+        if (cu == c) return;
+        int au = asg[cu];
+        if (au >= t) blocked = true;       // unassigned, or assigned in this very round
+        else if (lvl[cu] > m) m = lvl[cu];
+    });
+    if (blocked) blk[c] = t;
+    if (m >= 0) atomicMax(&cmax[c], m);
+}
+
+__global__ void k_lvl_assign(const int *list, int n, const int *__restrict__ label, int *lvl, int *asg,
+                             const int *cmax, const int *blk, int t, int *assigned)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int v = list[k];
+    if (label[v] != v || asg[v] != INF || blk[v] == t) return;
+    lvl[v] = cmax[v] + 1;
+    asg[v] = t;
+    atomicAdd(assigned, 1);
+}
+
+__global__ void k_node_level(long long SN, long long N, const int *__restrict__ label, const int *__restrict__ lvl,
+                             int *level, int *lmax)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= SN) return;
+    int L = lvl[label[v]];
+    level[v] = L;
+    long long a = v / N;
+    atomicMax(&lmax[a], L);
+}
+
+// sort key: (source, level) segment | component id (local smallest node) | node
+__global__ void k_keys(long long SN, long long N, int maxL, const int *__restrict__ label, const int *__restrict__ level,
+                       unsigned long long *keys)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= SN) return;
+    long long a = v / N;
+    unsigned long long seg = (unsigned long long)(a * maxL + level[v]);
+    unsigned long long comp = (unsigned long long)(label[v] - a * N);
+    unsigned long long node = (unsigned long long)(v - a * N);
+    keys[v] = (seg << 44) | (comp << 22) | node;
+}
+
+__global__ void k_perm(long long SN, long long N, int maxL, const unsigned long long *__restrict__ skeys,
+                       const int *__restrict__ label, const int *__restrict__ csize, int *perm, int *pos, int *lcount,
+                       int *head)
+{
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= SN) return;
+    unsigned long long key = skeys[p];
+    long long a = p / N, pl = p - a * N;
+    int node = (int)(key & ((1ull << 22) - 1));
+    int seg = (int)(key >> 44);
+    long long v = a * N + node;
+    bool member = csize[label[v]] > 1;
+    perm[p] = member ? ~node : node;
+    pos[v] = (int)pl;
+    atomicAdd(&lcount[seg], 1);
+    int is_head = 0;
+    if (member) {
+        if (pl == 0) is_head = 1;
+        else {
+            int prev = (int)(skeys[p - 1] & ((1ull << 22) - 1));
+            is_head = label[a * N + prev] != label[v];
+        }
+    }
+    head[p] = is_head;
+}
+
+// per position: forward edge count (external only for block members) and transposed count
+__global__ void k_counts(GridDesc g, long long SN, const int *__restrict__ perm, const int *__restrict__ label,
+                         const int *__restrict__ cnt, const int *__restrict__ nnode, const unsigned char *__restrict__ upmask,
+                         int *fcnt, int *tcnt)
+{
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= SN) return;
+    long long a = p / g.N;
+    int pn = perm[p];
+    bool member = pn < 0;
+    long long v = a * g.N + (member ? ~pn : pn);
+    const int slots = 2 * g.ndim;
+    int f = 0;
+    for (int e = 0; e < cnt[v]; ++e) {
+        long long u = a * g.N + nnode[v * slots + e];
+        if (!member || label[u] != label[v]) ++f;
+    }
+    int tc = 0;
+    for_succs(g, v, upmask, [&](long long u) { if (!member || label[u] != label[v]) ++tc; });
+    fcnt[p] = f;
+    tcnt[p] = tc;
+}
+
+__global__ void k_fill(GridDesc g, long long SN, const int *__restrict__ perm, const int *__restrict__ label,
+                       const int *__restrict__ cnt, const int *__restrict__ nnode, const double *__restrict__ nw,
+                       const unsigned char *__restrict__ upmask, const long long *__restrict__ fscan,
+                       const long long *__restrict__ tscan, const long long *__restrict__ fbase,
+                       const long long *__restrict__ tbase, int *rowptr, int *cptr, int *up_node, float *up_w32,
+                       double *up_w64, int *dn_node, float *dn_w32, double *dn_w64)
+{
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= SN) return;
+    long long a = p / g.N, pl = p - a * g.N;
+    int pn = perm[p];
+    bool member = pn < 0;
+    long long v = a * g.N + (member ? ~pn : pn);
+    const int slots = 2 * g.ndim;
+    long long fo = fscan[p], to = tscan[p];
+    rowptr[a * (g.N + 1) + pl] = (int)(fo - fbase[a]);
+    cptr[a * (g.N + 1) + pl] = (int)(to - tbase[a]);
+    if (pl == g.N - 1) {
+        rowptr[a * (g.N + 1) + g.N] = (int)(fbase[a + 1] - fbase[a]);
+        cptr[a * (g.N + 1) + g.N] = (int)(tbase[a + 1] - tbase[a]);
+    }
+    for (int e = 0; e < cnt[v]; ++e) {
+        int j = nnode[v * slots + e];
+        long long u = a * g.N + j;
+        if (member && label[u] == label[v]) continue;
+        double w = nw[v * slots + e];
+        up_node[fo] = j;
+        up_w64[fo] = w;
+        up_w32[fo] = (float)w;
+        ++fo;
+    }
+    const int self = (int)(v - a * g.N);
+    for_succs(g, v, upmask, [&](long long u) {
+        if (member && label[u] == label[v]) return;
+        double w = 0.0;
+        for (int e = 0; e < cnt[u]; ++e)
+            if (nnode[u * slots + e] == self) w = nw[u * slots + e];
+        dn_node[to] = (int)(u - a * g.N);
+        dn_w64[to] = w;
+        dn_w32[to] = (float)w;
+        ++to;
+    });
+}
+
+// calibration times model map, per position and per node (Sec. 3.2 and Sec. 2.3)
+__global__ void k_cq(long long SN, long long N, int model, const int *__restrict__ perm, const double *__restrict__ cs,
+                     const double *__restrict__ s, double *cq64, float *cq32, double *cqn64, float *cqn32)
+{
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= SN) return;
+    long long a = p / N, pl = p - a * N;
+    // natural-order entry for node pl
+    {
+        double si = s[pl];
+        double m = model == EIK_MODEL_SLOWNESS ? 1.0 : (model == EIK_MODEL_VELOCITY ? -(si * si) : -si);
+        double c = cs[p] * m;
+        cqn64[p] = c;
+        cqn32[p] = (float)c;
+    }
+    int pn = perm[p];
+    long long i = pn < 0 ? ~pn : pn;
+    double si = s[i];
+    double m = model == EIK_MODEL_SLOWNESS ? 1.0 : (model == EIK_MODEL_VELOCITY ? -(si * si) : -si);
+    double c = cs[a * N + i] * m;
+    cq64[p] = c;
+    cq32[p] = (float)c;
+}
+
+__global__ void k_rec_mark(int S, long long N, int n_rec, const int *__restrict__ rec, int *recpos, int *bad)
+{
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= (long long)S * n_rec) return;
+    long long a = k / n_rec;
+    int r = (int)(k - a * n_rec);
+    int node = rec[k];
+    if (node < 0 || node >= N) { atomicExch(bad, 1); return; }
+    if (atomicCAS(&recpos[a * N + node], -1, r) != -1) atomicExch(bad, 2);
+}
+
+__global__ void k_rec_slot(long long SN, long long N, const int *__restrict__ perm, const int *__restrict__ recpos,
+                           int *rec_slot)
+{
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= SN) return;
+    long long a = p / N;
+    int pn = perm[p];
+    rec_slot[p] = recpos[a * N + (pn < 0 ? ~pn : pn)];
+}
+
+// dense A_C = I - W_CC of every nontrivial block (nodes ascending = positions p0..p0+k-1)
+__global__ void k_block_fill(GridDesc g, const int4 *__restrict__ desc, const long long *__restrict__ off,
+                             const int *__restrict__ perm, const int *__restrict__ pos, const int *__restrict__ label,
+                             const int *__restrict__ cnt, const int *__restrict__ nnode, const double *__restrict__ nw,
+                             double *lu)
+{
+    int b = blockIdx.x;
+    int4 d = desc[b];
+    int a = d.x, p0 = d.y, k = d.z;
+    double *A = lu + off[3 * b + 0];
+    for (long long e = threadIdx.x; e < (long long)k * k; e += blockDim.x) A[e] = (e / k == e % k) ? 1.0 : 0.0;
+    __syncthreads();
+    const int slots = 2 * g.ndim;
+    for (int r = threadIdx.x; r < k; r += blockDim.x) {
+        long long v = a * g.N + ~perm[a * g.N + p0 + r];
+        for (int e = 0; e < cnt[v]; ++e) {
+            long long u = a * g.N + nnode[v * slots + e];
+            if (label[u] != label[v]) continue;
+            int c = pos[u] - p0;
+            A[(long long)r * k + c] -= nw[v * slots + e];
+        }
+    }
+}
+
+// Sec. 4.3: P_C A_C = L_C U_C with partial pivoting (first largest |a| on ties)
+__global__ void k_block_lu(const int4 *__restrict__ desc, const long long *__restrict__ off, double *lu, int *piv,
+                           double tol, int *err)
+{
+    int b = blockIdx.x;
+    int k = desc[b].z;
+    double *A = lu + off[3 * b + 0];
+    int *P = piv + off[3 * b + 1];
+    __shared__ double s_val[256];
+    __shared__ int s_idx[256];
+    __shared__ int s_p;
+    for (int r = 0; r < k; ++r) {
+        double best = -1.0;
+        int bi = k;
+        for (int t = r + threadIdx.x; t < k; t += blockDim.x) {
+            double x = fabs(A[(long long)t * k + r]);
+            if (x > best) { best = x; bi = t; }
+        }
+        s_val[threadIdx.x] = best;
+        s_idx[threadIdx.x] = bi;
+        __syncthreads();
+        for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+            if (threadIdx.x < h) {
+                double o = s_val[threadIdx.x + h];
+                int oi = s_idx[threadIdx.x + h];
+                if (o > s_val[threadIdx.x] || (o == s_val[threadIdx.x] && oi < s_idx[threadIdx.x])) {
+                    s_val[threadIdx.x] = o;
+                    s_idx[threadIdx.x] = oi;
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            s_p = s_idx[0];
+            P[r] = s_p;
+            if (!(s_val[0] >= tol)) atomicCAS(err, 0, DEV_SINGULAR);
+        }
+        __syncthreads();
+        int p = s_p;
+        if (p != r)
+            for (int c = threadIdx.x; c < k; c += blockDim.x) {
+                double x = A[(long long)r * k + c];
+                A[(long long)r * k + c] = A[(long long)p * k + c];
+                A[(long long)p * k + c] = x;
+            }
+        __syncthreads();
+        double pv = A[(long long)r * k + r];
+        for (int t = r + 1 + threadIdx.x; t < k; t += blockDim.x) A[(long long)t * k + r] /= pv;
+        __syncthreads();
+        long long rem = (long long)(k - r - 1) * (k - r - 1);
+        for (long long e = threadIdx.x; e < rem; e += blockDim.x) {
+            int t = r + 1 + (int)(e / (k - r - 1)), c = r + 1 + (int)(e % (k - r - 1));
+            A[(long long)t * k + c] -= A[(long long)t * k + r] * A[(long long)r * k + c];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_fill_inf(long long n, int *p)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v < n) p[v] = INF;
+}
+
+__global__ void k_check_assigned(long long SN, const int *label, const int *asg, int *bad)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= SN) return;
+    if (label[v] == v && asg[v] == INF) atomicAdd(bad, 1);
+}
+
+__global__ void k_count_roots(long long SN, long long N, const int *label, unsigned long long *nroots)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= SN) return;
+    if (label[v] == v) atomicAdd(&nroots[v / N], 1ull);
+}
+
+__global__ void k_count_edges(long long SN, long long N, const int *cnt, unsigned long long *ne)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= SN) return;
+    atomicAdd(&ne[v / N], (unsigned long long)cnt[v]);
+}
+
+__global__ void k_local_labels(long long SN, long long N, int *label)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= SN) return;
+    label[v] -= (int)((v / N) * N);
+}
+
+
+__global__ void k_compact_heads(long long SN, const int *head, const int *scan, int *hpos)
+{
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p < SN && head[p]) hpos[scan[p]] = (int)p;
+}
+
+__global__ void k_block_info(int nb, long long N, const int *hpos, const int *perm, const int *label, const int *level,
+                             const int *csize, int4 *info)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    long long p = hpos[b];
+    long long a = p / N;
+    long long v = a * N + ~perm[p];
+    info[b] = make_int4((int)a, (int)(p - a * N), csize[label[v]], level[v]);
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Scratch {
+    std::vector<void *> ptrs;
+    ~Scratch() { for (void *p : ptrs) cudaFree(p); }
+    template <typename T>
+    cudaError_t get(T **p, size_t n)
+    {
+        cudaError_t e = cudaMalloc((void **)p, std::max<size_t>(n, 1) * sizeof(T));
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+};
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n) { return cudaMalloc((void **)p, std::max<size_t>(n, 1) * sizeof(T)); }
+
+inline unsigned blocks_for(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void free_tangent(Tangent *t)
+{
+    if (!t) return;
+    void *ptrs[] = {t->perm, t->pos, t->label, t->level, t->rowptr, t->up_node, t->up_w32, t->up_w64, t->cptr,
+                    t->dn_node, t->dn_w32, t->dn_w64, t->cq64, t->cq32, t->cqn64, t->cqn32, t->rec_slot,
+                    t->rec_nat, t->nrow_cnt, t->nrow_node, t->nrow_w, t->cs_nat, t->blk_desc, t->blk_off, t->lu,
+                    t->piv, t->items_fwd, t->items_bwd, t->item_cnt, t->done, t->ticket, t->err, t->ws_vec,
+                    t->ws_blk, t->ebase_d, t->tbase_d};
+    for (void *p : ptrs) if (p) cudaFree(p);
+    delete t;
+}
+
+int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, const int *src_node,
+                  const int *rec_node, int n_rec, const eik_opts *opts, Tangent **out, cudaStream_t st)
+{
+    *out = nullptr;
+    GridDesc g = make_grid_desc(gin);
+    const long long N = g.N, SN = N * (long long)S;
+    const int nd = g.ndim, slots = 2 * nd;
+    if (N >= (1ll << 22)) { set_error("grid has %lld nodes; at most 2^22 - 1 supported", N); return EIK_ERR_INVALID; }
+    for (int a = 0; a < S; ++a)
+        if (src_node[a] < 0 || src_node[a] >= N) { set_error("source %d node %d out of range", a, src_node[a]); return EIK_ERR_INVALID; }
+
+    Tangent *t = new Tangent();
+    t->S = S; t->N = N; t->n_rec = n_rec; t->grid = g; t->opts = *opts; t->model = opts->model;
+    cudaGetDevice(&t->device);
+    cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, t->device);
+    auto fail = [&](int code) { free_tangent(t); return code; };
+#define TRY(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return fail(cuda_fail(e_, #call, __FILE__, __LINE__)); } while (0)
+
+    Scratch sc;
+    double *G, *gT;
+    int *cnt, *fst, *bst, *flags, *src_d, *lab, *act, *color, *inscc, *list, *csize, *lvl, *asg, *cmax, *blk, *lmax;
+    unsigned char *upmask;
+    unsigned long long *nid;
+    TRY(sc.get(&G, N * nd * nd));
+    TRY(sc.get(&gT, SN * nd));
+    TRY(sc.get(&upmask, SN));
+    TRY(sc.get(&fst, SN));
+    TRY(sc.get(&bst, SN));
+    TRY(sc.get(&flags, 8));
+    TRY(sc.get(&src_d, S));
+    TRY(sc.get(&nid, S));
+    TRY(dalloc(&t->nrow_cnt, SN));
+    TRY(dalloc(&t->nrow_node, SN * slots));
+    TRY(dalloc(&t->nrow_w, SN * slots));
+    TRY(dalloc(&t->cs_nat, SN));
+    TRY(dalloc(&t->label, SN));
+    TRY(dalloc(&t->level, SN));
+    cnt = t->nrow_cnt;
+    lab = t->label;
+    TRY(cudaMemcpyAsync(src_d, src_node, S * sizeof(int), cudaMemcpyHostToDevice, st));
+    TRY(cudaMemsetAsync(nid, 0, S * sizeof(unsigned long long), st));
+
+    // ---- metric, gradient, rows (Sec. 2.2, 3.1, 3.2)
+    k_metric<<<blocks_for(N), 256, 0, st>>>(g, gin->xyz, G, nullptr);
+    k_grad<<<blocks_for(SN), 256, 0, st>>>(g, S, T, gT);
+    k_assemble<<<blocks_for(SN), 256, 0, st>>>(g, S, G, gT, T, s, src_d, cnt, t->nrow_node, t->nrow_w, upmask,
+                                               t->cs_nat, nid);
+    TRY(cudaGetLastError());
+
+    // ---- forward and backward trimming (Sec. 3.5, Prop. 2)
+    int h_changed = 0;
+    int round = 0;
+    k_fill_inf<<<blocks_for(SN), 256, 0, st>>>(SN, fst);
+    k_fill_inf<<<blocks_for(SN), 256, 0, st>>>(SN, bst);
+    TRY(cudaGetLastError());
+    const int BATCH = 16;
+    for (;;) {
+        TRY(cudaMemsetAsync(flags, 0, sizeof(int), st));
+        for (int b = 0; b < BATCH; ++b, ++round) k_fwd_trim<<<blocks_for(SN), 256, 0, st>>>(g, SN, upmask, fst, round, flags);
+        TRY(cudaMemcpyAsync(&h_changed, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        if (!h_changed) break;
+    }
+    for (round = 0;;) {
+        TRY(cudaMemsetAsync(flags, 0, sizeof(int), st));
+        for (int b = 0; b < BATCH; ++b, ++round) k_bwd_trim<<<blocks_for(SN), 256, 0, st>>>(g, SN, upmask, fst, bst, round, flags);
+        TRY(cudaMemcpyAsync(&h_changed, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        if (!h_changed) break;
+    }
+
+    // ---- SCCs of the trimmed residual by colouring (Sec. 4.1)
+    TRY(sc.get(&act, SN));
+    TRY(sc.get(&color, SN));
+    TRY(sc.get(&inscc, SN));
+    TRY(sc.get(&list, SN));
+    TRY(cudaMemsetAsync(flags, 0, 8 * sizeof(int), st));
+    k_collect<<<blocks_for(SN), 256, 0, st>>>(SN, fst, bst, list, flags + 1, lab, act);
+    int nres = 0;
+    TRY(cudaMemcpyAsync(&nres, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    int outer = 0;
+    while (nres > 0) {
+        if (++outer > 1000000) { set_error("SCC colouring did not terminate"); return fail(EIK_ERR_CYCLE); }
+        k_color_init<<<blocks_for(nres), 256, 0, st>>>(list, nres, act, color, inscc);
+        for (;;) {
+            TRY(cudaMemsetAsync(flags, 0, sizeof(int), st));
+            for (int b = 0; b < 8; ++b) k_color_prop<<<blocks_for(nres), 256, 0, st>>>(g, list, nres, upmask, act, color, flags);
+            TRY(cudaMemcpyAsync(&h_changed, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+            TRY(cudaStreamSynchronize(st));
+            if (!h_changed) break;
+        }
+        k_scc_roots<<<blocks_for(nres), 256, 0, st>>>(list, nres, act, color, inscc);
+        for (;;) {
+            TRY(cudaMemsetAsync(flags, 0, sizeof(int), st));
+            for (int b = 0; b < 8; ++b) k_scc_back<<<blocks_for(nres), 256, 0, st>>>(g, list, nres, upmask, act, color, inscc, flags);
+            TRY(cudaMemcpyAsync(&h_changed, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+            TRY(cudaStreamSynchronize(st));
+            if (!h_changed) break;
+        }
+        TRY(cudaMemsetAsync(flags + 2, 0, sizeof(int), st));
+        k_scc_take<<<blocks_for(nres), 256, 0, st>>>(list, nres, act, color, inscc, lab, flags + 2);
+        int rem = 0;
+        TRY(cudaMemcpyAsync(&rem, flags + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        if (rem == 0) break;
+    }
+    TRY(sc.get(&csize, SN));
+    TRY(cudaMemsetAsync(csize, 0, SN * sizeof(int), st));
+    k_comp_size<<<blocks_for(SN), 256, 0, st>>>(SN, lab, csize);
+
+    // ---- canonical levels (longest path on the condensation)
+    TRY(sc.get(&lvl, SN));
+    TRY(sc.get(&asg, SN));
+    TRY(sc.get(&cmax, SN));
+    TRY(sc.get(&blk, SN));
+    TRY(sc.get(&lmax, S));
+    TRY(cudaMemsetAsync(flags, 0, 8 * sizeof(int), st));
+    k_lvl_init<<<blocks_for(SN), 256, 0, st>>>(SN, fst, lab, lvl, asg, cmax, blk, list, flags + 1);
+    int nlst = 0;
+    TRY(cudaMemcpyAsync(&nlst, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    for (round = 0; nlst > 0;) {
+        TRY(cudaMemsetAsync(flags + 3, 0, sizeof(int), st));
+        for (int b = 0; b < BATCH; ++b, ++round) {
+            k_lvl_scan<<<blocks_for(nlst), 256, 0, st>>>(g, list, nlst, upmask, lab, lvl, asg, cmax, blk, round);
+            k_lvl_assign<<<blocks_for(nlst), 256, 0, st>>>(list, nlst, lab, lvl, asg, cmax, blk, round, flags + 3);
+        }
+        int assigned = 0;
+        TRY(cudaMemcpyAsync(&assigned, flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        if (assigned == 0) break;
+        if (round > 100000000) { set_error("level rounds did not terminate"); return fail(EIK_ERR_CYCLE); }
+    }
+    // check every component assigned
+    TRY(cudaMemsetAsync(flags + 4, 0, sizeof(int), st));
+    k_check_assigned<<<blocks_for(SN), 256, 0, st>>>(SN, lab, asg, flags + 4);
+    TRY(cudaMemsetAsync(lmax, 0, S * sizeof(int), st));
+    k_node_level<<<blocks_for(SN), 256, 0, st>>>(SN, N, lab, lvl, t->level, lmax);
+    int unassigned = 0;
+    std::vector<int> hlmax(S);
+    TRY(cudaMemcpyAsync(&unassigned, flags + 4, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRY(cudaMemcpyAsync(hlmax.data(), lmax, S * sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    if (unassigned) { set_error("condensation has a cycle (%d components unassigned)", unassigned); return fail(EIK_ERR_CYCLE); }
+    t->nlev.resize(S);
+    int maxL = 0;
+    for (int a = 0; a < S; ++a) { t->nlev[a] = hlmax[a] + 1; maxL = std::max(maxL, t->nlev[a]); }
+    t->maxL = maxL;
+    int segbits = 1;
+    while ((1ll << segbits) < (long long)S * maxL) ++segbits;
+    if (segbits > 20) { set_error("too many (source, level) segments"); return fail(EIK_ERR_INVALID); }
+
+    // ---- canonical order: sort by (source, level, component, node)
+    unsigned long long *keys, *skeys;
+    int *lcount, *head;
+    TRY(sc.get(&keys, SN));
+    TRY(sc.get(&skeys, SN));
+    TRY(sc.get(&lcount, (size_t)S * maxL));
+    TRY(sc.get(&head, SN));
+    TRY(dalloc(&t->perm, SN));
+    TRY(dalloc(&t->pos, SN));
+    k_keys<<<blocks_for(SN), 256, 0, st>>>(SN, N, maxL, lab, t->level, keys);
+    {
+        size_t tb = 0;
+        TRY(cub::DeviceRadixSort::SortKeys(nullptr, tb, keys, skeys, (int64_t)SN, 0, 44 + segbits, st));
+        void *tmp;
+        TRY(sc.get((char **)&tmp, tb));
+        TRY(cub::DeviceRadixSort::SortKeys(tmp, tb, keys, skeys, (int64_t)SN, 0, 44 + segbits, st));
+    }
+    TRY(cudaMemsetAsync(lcount, 0, (size_t)S * maxL * sizeof(int), st));
+    k_perm<<<blocks_for(SN), 256, 0, st>>>(SN, N, maxL, skeys, lab, csize, t->perm, t->pos, lcount, head);
+    TRY(cudaGetLastError());
+    std::vector<int> hl((size_t)S * maxL);
+    TRY(cudaMemcpyAsync(hl.data(), lcount, hl.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+
+    // ---- rows in canonical order (gather form) and transposed rows
+    int *fcnt, *tcnt;
+    long long *fscan, *tscan;
+    TRY(sc.get(&fcnt, SN));
+    TRY(sc.get(&tcnt, SN));
+    TRY(sc.get(&fscan, SN + 1));
+    TRY(sc.get(&tscan, SN + 1));
+    k_counts<<<blocks_for(SN), 256, 0, st>>>(g, SN, t->perm, lab, cnt, t->nrow_node, upmask, fcnt, tcnt);
+    {
+        size_t tb = 0, tb2 = 0;
+        TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb, fcnt, fscan, (int64_t)SN + 1, st));
+        TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb2, tcnt, tscan, (int64_t)SN + 1, st));
+        tb = std::max(tb, tb2);
+        void *tmp;
+        TRY(sc.get((char **)&tmp, tb));
+        // counts arrays are SN long; the (SN+1)-th input must be 0: use SN items, total appended below
+        TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, fcnt, fscan, (int64_t)SN, st));
+        TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, tcnt, tscan, (int64_t)SN, st));
+    }
+    // per-source bases (host)
+    std::vector<long long> hf(S + 1), ht(S + 1);
+    {
+        for (int a = 0; a < S; ++a) {
+            TRY(cudaMemcpyAsync(&hf[a], fscan + (long long)a * N, sizeof(long long), cudaMemcpyDeviceToHost, st));
+            TRY(cudaMemcpyAsync(&ht[a], tscan + (long long)a * N, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        }
+        long long lf = 0, lt = 0;
+        int cf = 0, ct = 0;
+        TRY(cudaMemcpyAsync(&lf, fscan + SN - 1, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        TRY(cudaMemcpyAsync(&lt, tscan + SN - 1, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        TRY(cudaMemcpyAsync(&cf, fcnt + SN - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TRY(cudaMemcpyAsync(&ct, tcnt + SN - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        hf[S] = lf + cf;
+        ht[S] = lt + ct;
+    }
+    for (int a = 0; a < S; ++a)
+        if (hf[a + 1] - hf[a] >= (1ll << 31) || ht[a + 1] - ht[a] >= (1ll << 31)) {
+            set_error("too many edges per source"); return fail(EIK_ERR_INVALID);
+        }
+    t->ebase = hf;
+    t->tbase = ht;
+    TRY(dalloc(&t->ebase_d, S + 1));
+    TRY(dalloc(&t->tbase_d, S + 1));
+    long long *fbase_d = t->ebase_d, *tbase_d = t->tbase_d;
+    TRY(cudaMemcpyAsync(fbase_d, hf.data(), (S + 1) * sizeof(long long), cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(tbase_d, ht.data(), (S + 1) * sizeof(long long), cudaMemcpyHostToDevice, st));
+    TRY(dalloc(&t->rowptr, (size_t)S * (N + 1)));
+    TRY(dalloc(&t->cptr, (size_t)S * (N + 1)));
+    TRY(dalloc(&t->up_node, hf[S]));
+    TRY(dalloc(&t->up_w32, hf[S]));
+    TRY(dalloc(&t->up_w64, hf[S]));
+    TRY(dalloc(&t->dn_node, ht[S]));
+    TRY(dalloc(&t->dn_w32, ht[S]));
+    TRY(dalloc(&t->dn_w64, ht[S]));
+    k_fill<<<blocks_for(SN), 256, 0, st>>>(g, SN, t->perm, lab, cnt, t->nrow_node, t->nrow_w, upmask, fscan, tscan,
+                                           fbase_d, tbase_d, t->rowptr, t->cptr, t->up_node, t->up_w32, t->up_w64,
+                                           t->dn_node, t->dn_w32, t->dn_w64);
+    TRY(cudaGetLastError());
+
+    // ---- C*M coefficients, receivers
+    TRY(dalloc(&t->cq64, SN));
+    TRY(dalloc(&t->cq32, SN));
+    TRY(dalloc(&t->cqn64, SN));
+    TRY(dalloc(&t->cqn32, SN));
+    k_cq<<<blocks_for(SN), 256, 0, st>>>(SN, N, t->model, t->perm, t->cs_nat, s, t->cq64, t->cq32, t->cqn64, t->cqn32);
+    int *recpos;
+    TRY(sc.get(&recpos, SN));
+    TRY(cudaMemsetAsync(recpos, 0xff, SN * sizeof(int), st));
+    TRY(dalloc(&t->rec_slot, SN));
+    TRY(dalloc(&t->rec_nat, (size_t)S * std::max(n_rec, 1)));
+    if (n_rec > 0) {
+        TRY(cudaMemcpyAsync(t->rec_nat, rec_node, (size_t)S * n_rec * sizeof(int), cudaMemcpyHostToDevice, st));
+        TRY(cudaMemsetAsync(flags + 5, 0, sizeof(int), st));
+        k_rec_mark<<<blocks_for((long long)S * n_rec), 256, 0, st>>>(S, N, n_rec, t->rec_nat, recpos, flags + 5);
+        int bad = 0;
+        TRY(cudaMemcpyAsync(&bad, flags + 5, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        if (bad) {
+            set_error(bad == 1 ? "receiver node out of range" : "duplicate receiver node within a source");
+            return fail(EIK_ERR_INVALID);
+        }
+    }
+    k_rec_slot<<<blocks_for(SN), 256, 0, st>>>(SN, N, t->perm, recpos, t->rec_slot);
+
+    // ---- level pointers (host) and blocks
+    t->level_ptr.assign((size_t)S * (maxL + 1), 0);
+    for (int a = 0; a < S; ++a) {
+        long long acc = 0;
+        for (int L = 0; L <= maxL; ++L) {
+            t->level_ptr[(size_t)a * (maxL + 1) + L] = acc;
+            if (L < maxL) acc += hl[(size_t)a * maxL + L];
+        }
+    }
+    {
+        int *hpos, *hscan;
+        TRY(sc.get(&hpos, SN));
+        TRY(sc.get(&hscan, SN));
+        size_t tb = 0;
+        TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb, head, hscan, (int64_t)SN, st));
+        void *tmp;
+        TRY(sc.get((char **)&tmp, tb));
+        TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, head, hscan, (int64_t)SN, st));
+        k_compact_heads<<<blocks_for(SN), 256, 0, st>>>(SN, head, hscan, hpos);
+        int nb = 0, lastflag = 0;
+        TRY(cudaMemcpyAsync(&nb, hscan + SN - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TRY(cudaMemcpyAsync(&lastflag, head + SN - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        nb += lastflag;
+        int4 *binfo;
+        TRY(sc.get(&binfo, std::max(nb, 1)));
+        if (nb > 0) k_block_info<<<blocks_for(nb), 256, 0, st>>>(nb, N, hpos, t->perm, lab, t->level, csize, binfo);
+        std::vector<int4> hb(std::max(nb, 1));
+        TRY(cudaMemcpyAsync(hb.data(), binfo, std::max(nb, 1) * sizeof(int4), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        t->nblk = nb;
+        long long lo = 0, po = 0, wo = 0;
+        std::vector<int4> hd(std::max(nb, 1));
+        std::vector<long long> ho(3 * std::max(nb, 1));
+        for (int b = 0; b < nb; ++b) {
+            Block B;
+            B.src = hb[b].x;
+            B.p0 = hb[b].y;
+            B.k = hb[b].z;
+            B.level = hb[b].w;
+            B.lu = lo; B.piv = po; B.ws = wo;
+            lo += (long long)B.k * B.k; po += B.k; wo += B.k;
+            t->blocks.push_back(B);
+            hd[b] = make_int4(B.src, B.p0, B.k, B.level);
+            ho[3 * b] = B.lu; ho[3 * b + 1] = B.piv; ho[3 * b + 2] = B.ws;
+        }
+        t->lu_words = lo; t->piv_words = po; t->ws_rows = wo;
+        TRY(dalloc(&t->blk_desc, std::max(nb, 1)));
+        TRY(dalloc(&t->blk_off, 3 * std::max(nb, 1)));
+        TRY(dalloc(&t->lu, std::max(lo, 1ll)));
+        TRY(dalloc(&t->piv, std::max(po, 1ll)));
+        TRY(dalloc(&t->err, 4));
+        TRY(cudaMemsetAsync(t->err, 0, 4 * sizeof(int), st));
+        if (nb > 0) {
+            TRY(cudaMemcpyAsync(t->blk_desc, hd.data(), nb * sizeof(int4), cudaMemcpyHostToDevice, st));
+            TRY(cudaMemcpyAsync(t->blk_off, ho.data(), 3 * nb * sizeof(long long), cudaMemcpyHostToDevice, st));
+            k_block_fill<<<nb, 256, 0, st>>>(g, t->blk_desc, t->blk_off, t->perm, t->pos, lab, cnt, t->nrow_node,
+                                             t->nrow_w, t->lu);
+            k_block_lu<<<nb, 256, 0, st>>>(t->blk_desc, t->blk_off, t->lu, t->piv, opts->lu_pivot_tol, t->err);
+            TRY(cudaGetLastError());
+            int e = 0;
+            TRY(cudaMemcpyAsync(&e, t->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+            TRY(cudaStreamSynchronize(st));
+            if (e == DEV_SINGULAR) { set_error("an SCC block is singular (pivot below %g)", opts->lu_pivot_tol); return fail(EIK_ERR_SINGULAR_BLOCK); }
+        }
+    }
+
+    // ---- traversal work items: level-major over sources
+    {
+        int chunk = opts->chunk > 0 ? opts->chunk : 64;
+        std::vector<std::vector<int4>> per((size_t)S * maxL);
+        std::vector<int> blk_ptr(S + 1, 0);
+        // blocks are ordered by (source, position), hence by (source, level)
+        size_t bi = 0;
+        for (int a = 0; a < S; ++a) {
+            for (int L = 0; L < t->nlev[a]; ++L) {
+                long long p0 = t->level_ptr[(size_t)a * (maxL + 1) + L], p1 = t->level_ptr[(size_t)a * (maxL + 1) + L + 1];
+                auto &vec = per[(size_t)a * maxL + L];
+                for (long long p = p0; p < p1; p += chunk)
+                    vec.push_back(make_int4(a, L, (int)p, (int)std::min(p1, p + chunk)));
+                while (bi < t->blocks.size() && t->blocks[bi].src == a && t->blocks[bi].level == L) {
+                    vec.push_back(make_int4(a, L, ~(int)bi, 0));
+                    ++bi;
+                }
+            }
+        }
+        std::vector<int4> fw, bw;
+        std::vector<int> icnt(2 * (size_t)S * maxL, 0);
+        t->step_ptr_fwd.assign(maxL + 1, 0);
+        t->step_ptr_bwd.assign(maxL + 1, 0);
+        for (int stp = 0; stp < maxL; ++stp) {
+            t->step_ptr_fwd[stp] = (int)fw.size();
+            t->step_ptr_bwd[stp] = (int)bw.size();
+            for (int a = 0; a < S; ++a) {
+                if (stp >= t->nlev[a]) continue;
+                for (int4 it : per[(size_t)a * maxL + stp]) { it.y = stp; fw.push_back(it); }
+                icnt[(size_t)a * maxL + stp] = (int)per[(size_t)a * maxL + stp].size();
+                int L = t->nlev[a] - 1 - stp;
+                for (int4 it : per[(size_t)a * maxL + L]) { it.y = stp; bw.push_back(it); }
+                icnt[(size_t)S * maxL + (size_t)a * maxL + stp] = (int)per[(size_t)a * maxL + L].size();
+            }
+        }
+        t->step_ptr_fwd[maxL] = (int)fw.size();
+        t->step_ptr_bwd[maxL] = (int)bw.size();
+        t->nitems = (int)fw.size();
+        TRY(dalloc(&t->items_fwd, fw.size()));
+        TRY(dalloc(&t->items_bwd, bw.size()));
+        TRY(dalloc(&t->item_cnt, icnt.size()));
+        TRY(dalloc(&t->done, icnt.size()));
+        TRY(dalloc(&t->ticket, 4));
+        TRY(cudaMemcpyAsync(t->items_fwd, fw.data(), fw.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+        TRY(cudaMemcpyAsync(t->items_bwd, bw.data(), bw.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+        TRY(cudaMemcpyAsync(t->item_cnt, icnt.data(), icnt.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    }
+
+    // ---- statistics
+    {
+        std::vector<unsigned long long> hid(S);
+        TRY(cudaMemcpyAsync(hid.data(), nid, S * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        unsigned long long *nroots;
+        TRY(sc.get(&nroots, S));
+        TRY(cudaMemsetAsync(nroots, 0, S * sizeof(unsigned long long), st));
+        k_count_roots<<<blocks_for(SN), 256, 0, st>>>(SN, N, lab, nroots);
+        std::vector<unsigned long long> hr(S);
+        TRY(cudaMemcpyAsync(hr.data(), nroots, S * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        t->stats.assign(S, eik_stats{});
+        for (int a = 0; a < S; ++a) {
+            eik_stats &x = t->stats[a];
+            x.nodes = N;
+            x.components = (int64_t)hr[a];
+            x.levels = t->nlev[a];
+            long long w = 0;
+            for (int L = 0; L < t->nlev[a]; ++L) w = std::max(w, (long long)hl[(size_t)a * maxL + L]);
+            x.max_level_width = w;
+            x.identity_rows = (int64_t)hid[a];
+        }
+        for (const Block &B : t->blocks) {
+            eik_stats &x = t->stats[B.src];
+            x.nontrivial += 1;
+            x.cyclic_nodes += B.k;
+            x.largest = std::max<int64_t>(x.largest, B.k);
+            x.lu_doubles += (int64_t)B.k * B.k;
+        }
+        // edges: full rows (natural)
+        unsigned long long *ne;
+        TRY(sc.get(&ne, S));
+        TRY(cudaMemsetAsync(ne, 0, S * sizeof(unsigned long long), st));
+        k_count_edges<<<blocks_for(SN), 256, 0, st>>>(SN, N, cnt, ne);
+        std::vector<unsigned long long> hne(S);
+        TRY(cudaMemcpyAsync(hne.data(), ne, S * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        for (int a = 0; a < S; ++a) t->stats[a].edges = (int64_t)hne[a];
+    }
+    // convert labels to local ids for export
+    k_local_labels<<<blocks_for(SN), 256, 0, st>>>(SN, N, lab);
+    TRY(cudaGetLastError());
+    TRY(cudaStreamSynchronize(st));
+#undef TRY
+    *out = t;
+    return EIK_OK;
+}
+
+}  // namespace eik

@@ -1,0 +1,255 @@
+"""Thin Python binding of libeik (include/eik.h): argument marshalling only.
+
+Every call passes device pointers of torch CUDA tensors and torch's current CUDA
+stream to the C-ABI; all arithmetic runs in the library's CUDA kernels.  There is no
+CPU or PyTorch fallback: without the built library (libeik.so next to this file) or
+without a CUDA device every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libeik.so")
+
+EIK_F64, EIK_F32 = 0, 1
+MODEL_SLOWNESS, MODEL_VELOCITY, MODEL_RELATIVE = 0, 1, 2
+SCHED_PERSISTENT, SCHED_LEVELS = 0, 1
+STATUS = {0: "OK", -1: "INVALID", -2: "OOM", -3: "SINGULAR_BLOCK", -4: "NOT_CONVERGED", -5: "TIMEOUT",
+          -6: "CUDA", -7: "CYCLE"}
+
+EXPORTED = ["eik_opts_default", "eik_last_error", "eik_version", "eik_forward", "tangent_build", "tangent_apply",
+            "tangent_apply_T", "tangent_solve", "tangent_solve_T", "tangent_stats", "tangent_dims",
+            "tangent_export", "tangent_status", "tangent_free", "sweep_apply", "tangent_debug_hold"]
+
+
+class EikError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libeik {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Grid_(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("n", C.c_int * 3), ("dxi", C.c_double * 3), ("xyz", C.c_void_p)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("model", C.c_int), ("lu_pivot_tol", C.c_double), ("schedule", C.c_int), ("threads", C.c_int),
+                ("chunk", C.c_int), ("ctas_per_sm", C.c_int), ("wait_timeout_s", C.c_double),
+                ("eik_tol", C.c_double), ("eik_max_cycles", C.c_int), ("eik_src_radius", C.c_double),
+                ("sweep_tol", C.c_double), ("sweep_max_cycles", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("nodes", "edges", "components", "nontrivial", "cyclic_nodes", "largest",
+                                         "levels", "max_level_width", "identity_rows", "lu_doubles")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libeik.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run `python -m paper_2609_14982_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        P, I, D = C.c_void_p, C.c_int, C.c_double
+        L.eik_opts_default.argtypes = [C.POINTER(Opts)]
+        L.eik_last_error.restype = C.c_char_p
+        L.eik_version.restype = C.c_char_p
+        L.eik_forward.argtypes = [C.POINTER(Grid_), P, I, P, P, C.POINTER(Opts), C.POINTER(I), P]
+        L.tangent_build.argtypes = [C.POINTER(Grid_), P, P, I, P, P, I, C.POINTER(Opts), C.POINTER(P), P]
+        L.tangent_apply.argtypes = [P, P, I, I, P, P, I, P]
+        L.tangent_apply_T.argtypes = [P, P, I, I, P, P, I, P]
+        L.tangent_solve.argtypes = [P, P, I, P, I, P]
+        L.tangent_solve_T.argtypes = [P, P, I, P, I, P]
+        L.tangent_stats.argtypes = [P, I, C.POINTER(Stats)]
+        L.tangent_dims.argtypes = [P, C.POINTER(I), C.POINTER(C.c_int64), C.POINTER(I)]
+        L.tangent_export.argtypes = [P, I, P, P, P, P, P, P, P, P]
+        L.tangent_status.argtypes = [P, P]
+        L.tangent_free.argtypes = [P]
+        L.tangent_free.restype = None
+        L.tangent_debug_hold.argtypes = [P, I, I]
+        L.sweep_apply.argtypes = [P, I, P, I, P, I, C.POINTER(Opts), C.POINTER(I), P]
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise EikError(rc, lib().eik_last_error().decode())
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().eik_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype=None, name="tensor") -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def _dt(dtype) -> int:
+    if dtype == torch.float64:
+        return EIK_F64
+    if dtype == torch.float32:
+        return EIK_F32
+    raise TypeError("dtype must be float32 or float64")
+
+
+class DeviceGrid:
+    """A workload grid on the device (xyz float64 [N, ndim])."""
+
+    def __init__(self, grid, device="cuda"):
+        self.host = grid
+        self.ndim = grid.ndim
+        self.n = tuple(grid.n)
+        self.N = grid.N
+        self.xyz = torch.as_tensor(grid.xyz, dtype=torch.float64, device=device).contiguous()
+        self.c = Grid_()
+        self.c.ndim = grid.ndim
+        for d in range(3):
+            self.c.n[d] = grid.n[d] if d < grid.ndim else 1
+            self.c.dxi[d] = grid.dxi[d] if d < grid.ndim else 1.0
+        self.c.xyz = self.xyz.data_ptr()
+
+
+def eik_forward(dgrid: DeviceGrid, s: torch.Tensor, src, opts: Opts | None = None, out: torch.Tensor | None = None):
+    """First-arrival traveltimes [S, N] (float64) for the given source nodes."""
+    src = torch.as_tensor(src, dtype=torch.int32).contiguous().cpu()
+    S = int(src.numel())
+    if out is None:
+        out = torch.empty((S, dgrid.N), dtype=torch.float64, device=s.device)
+    cyc = C.c_int(0)
+    _check(lib().eik_forward(C.byref(dgrid.c), _dev(s, torch.float64, "s"), S, C.c_void_p(src.data_ptr()),
+                             _dev(out, torch.float64, "T"), C.byref(opts) if opts else None, C.byref(cyc), _stream()))
+    return out, cyc.value
+
+
+class Tangent:
+    """The frozen per-source states S_a of all sources (owned by libeik)."""
+
+    def __init__(self, dgrid: DeviceGrid, T: torch.Tensor, s: torch.Tensor, src, rec=None, opts: Opts | None = None):
+        src = torch.as_tensor(src, dtype=torch.int32).contiguous().cpu()
+        self.S = int(src.numel())
+        if rec is None:
+            rec = torch.zeros((self.S, 0), dtype=torch.int32)
+        rec = torch.as_tensor(rec, dtype=torch.int32).cpu()
+        if rec.dim() == 1:
+            rec = rec.unsqueeze(0).expand(self.S, -1)
+        rec = rec.contiguous()
+        self.n_rec = int(rec.shape[1])
+        self.N = dgrid.N
+        self.dgrid = dgrid
+        self.opts = opts if opts is not None else default_opts()
+        h = C.c_void_p()
+        _check(lib().tangent_build(C.byref(dgrid.c), _dev(T, torch.float64, "T"), _dev(s, torch.float64, "s"),
+                                   self.S, C.c_void_p(src.data_ptr()),
+                                   C.c_void_p(rec.data_ptr()) if self.n_rec else None, self.n_rec,
+                                   C.byref(self.opts), C.byref(h), _stream()))
+        self.h = h
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().tangent_free(self.h)
+            self.h = C.c_void_p()
+
+    # ---- Jacobian actions
+    def apply(self, p: torch.Tensor, shared_model: bool, dT_full=None, d_rec=None):
+        """J p: p [N, R] (shared) or [S, N, R]; returns (dT_full, d_rec)."""
+        R = p.shape[-1]
+        if d_rec is None and self.n_rec:
+            d_rec = torch.empty((self.S, self.n_rec, R), dtype=p.dtype, device=p.device)
+        _check(lib().tangent_apply(self.h, _dev(p, name="p"), int(shared_model), R,
+                                   _dev(dT_full, p.dtype, "dT_full") if dT_full is not None else None,
+                                   _dev(d_rec, p.dtype, "d_rec") if d_rec is not None else None, _dt(p.dtype),
+                                   _stream()))
+        return dT_full, d_rec
+
+    def apply_T(self, y: torch.Tensor, sum_sources: bool = True, g=None, lam_full=None):
+        """J^T y: y [S, n_rec, R]; returns (g, lam_full)."""
+        R = y.shape[-1]
+        if g is None:
+            shape = (self.N, R) if sum_sources else (self.S, self.N, R)
+            g = torch.empty(shape, dtype=y.dtype, device=y.device)
+        _check(lib().tangent_apply_T(self.h, _dev(y, name="y"), R, int(sum_sources), _dev(g, y.dtype, "g"),
+                                     _dev(lam_full, y.dtype, "lam_full") if lam_full is not None else None,
+                                     _dt(y.dtype), _stream()))
+        return g, lam_full
+
+    def solve(self, q: torch.Tensor, out=None):
+        """A^-1 q for every source: q [S, N, R]."""
+        out = torch.empty_like(q) if out is None else out
+        _check(lib().tangent_solve(self.h, _dev(q, name="q"), q.shape[-1], _dev(out, q.dtype, "x"), _dt(q.dtype),
+                                   _stream()))
+        return out
+
+    def solve_T(self, r: torch.Tensor, out=None):
+        out = torch.empty_like(r) if out is None else out
+        _check(lib().tangent_solve_T(self.h, _dev(r, name="r"), r.shape[-1], _dev(out, r.dtype, "x"), _dt(r.dtype),
+                                     _stream()))
+        return out
+
+    def sweep(self, b: torch.Tensor, transpose=False, opts: Opts | None = None, out=None):
+        """Directional Gauss-Seidel sweeping of the same operator; returns (x, cycles)."""
+        out = torch.empty_like(b) if out is None else out
+        cyc = C.c_int(0)
+        _check(lib().sweep_apply(self.h, int(transpose), _dev(b, name="b"), b.shape[-1], _dev(out, b.dtype, "x"),
+                                 _dt(b.dtype), C.byref(opts) if opts else None, C.byref(cyc), _stream()))
+        return out, cyc.value
+
+    def debug_hold(self, source: int, step: int):
+        """Test hook: make the persistent traversal's wait before (source, step) run out."""
+        _check(lib().tangent_debug_hold(self.h, source, step))
+
+    # ---- structure
+    def status(self):
+        _check(lib().tangent_status(self.h, _stream()))
+
+    def stats(self, a: int) -> dict:
+        st = Stats()
+        _check(lib().tangent_stats(self.h, a, C.byref(st)))
+        return st.as_dict()
+
+    def export(self, a: int) -> dict:
+        import numpy as np
+        st = self.stats(a)
+        N = self.N
+        label = np.zeros(N, dtype=np.int32)
+        level = np.zeros(N, dtype=np.int32)
+        perm = np.zeros(N, dtype=np.int32)
+        level_ptr = np.zeros(st["levels"] + 1, dtype=np.int64)
+        row_ptr = np.zeros(N + 1, dtype=np.int64)
+        col = np.zeros(max(st["edges"], 1), dtype=np.int32)
+        w = np.zeros(max(st["edges"], 1), dtype=np.float64)
+        cs = np.zeros(N, dtype=np.float64)
+        ptrs = [x.ctypes.data_as(C.c_void_p) for x in (label, level, perm, level_ptr, row_ptr, col, w, cs)]
+        _check(lib().tangent_export(self.h, a, *ptrs))
+        return dict(label=label, level=level, perm=perm, level_ptr=level_ptr, row_ptr=row_ptr,
+                    col=col[:st["edges"]], w=w[:st["edges"]], cs=cs, stats=st)

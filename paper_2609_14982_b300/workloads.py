@@ -178,6 +178,20 @@ def curved_state(g: Grid, src: int, eps: float) -> StateCase:
     return StateCase(g, s, T, src)
 
 
+def skew_box_grid(n, L=6.0, H=4.0, amp=0.4) -> Grid:
+    """2-D convex box [0, L] x [0, H] with a non-orthogonal interior map (the boundary is
+    mapped onto itself): x = xi + amp sin(pi zeta/H) sin(2 pi xi/L),
+    z = zeta + amp/2 sin(pi xi/L) sin(2 pi zeta/H).  Straight and curved rays of a
+    constant-gradient medium stay inside, so its closed form holds on the domain."""
+    xi = np.linspace(0.0, L, n[0])
+    ze = np.linspace(0.0, H, n[1])
+    X, Z = np.meshgrid(xi, ze, indexing="ij")
+    x = X + amp * np.sin(np.pi * Z / H) * np.sin(2 * np.pi * X / L)
+    z = Z + 0.5 * amp * np.sin(np.pi * X / L) * np.sin(2 * np.pi * Z / H)
+    xyz = np.ascontiguousarray(np.stack([x.ravel(), z.ravel()], axis=1))
+    return Grid(2, tuple(n), (L / (n[0] - 1), H / (n[1] - 1)), xyz, (0.0, 0.0), H)
+
+
 # ---------------------------------------------------------------------------
 # Constant-gradient medium v = v0 + g z: closed-form first arrival
 # ---------------------------------------------------------------------------

@@ -224,3 +224,41 @@ def test_singular_block_detected(oracle_mod):
     A = np.array([[1.0, -1.0], [-1.0, 1.0]])
     piv = np.zeros(2, dtype=np.int32)
     assert O.lib().or_lu(2, A.reshape(-1).copy(), piv) == 2
+
+
+def test_state_homogeneous_fixed_point(oracle_mod):
+    """State reading (Sec. 2.1-2.2): in a homogeneous medium tau = 1 is the discrete fixed
+    point, so T = s |x - x_s| on the deformed grid to rounding, after one cycle."""
+    O = oracle_mod
+    g = W.table1_grid(21)
+    src = g.index(10, 10, 0)
+    T, cyc = O.eik_forward(g, np.full(g.N, 1.0 / 3000.0), src)
+    ref = np.sqrt(((g.xyz - g.xyz[src]) ** 2).sum(1)) / 3000.0
+    assert cyc == 1 and np.max(np.abs(T - ref)) <= 1e-15
+
+
+def test_state_first_order_on_skewed_box(oracle_mod):
+    """State reading: against the constant-gradient closed form on a convex box with a
+    non-orthogonal interior map the max error halves with h (first order)."""
+    O = oracle_mod
+    errs = []
+    for m in (1, 2, 4):
+        g = W.skew_box_grid((30 * m + 1, 20 * m + 1))
+        v = 1.5 + 0.5 * g.xyz[:, 1]
+        src = g.index(10 * m, 5 * m)
+        T, cyc = O.eik_forward(g, 1.0 / v, src)
+        assert cyc > 0
+        Tex = W.linear_velocity_T(g.xyz, g.xyz[src], 1.5, 0.5)
+        errs.append(np.max(np.abs(T - Tex)) / Tex.max())
+    assert errs[0] < 0.03
+    for a, b in zip(errs, errs[1:]):
+        assert 1.8 < a / b < 2.3
+
+
+def test_state_converges_on_topography_3d(oracle_mod):
+    """State reading: the sweeping converges on a 3-D workload recipe with topography."""
+    O = oracle_mod
+    g, _ = W._config3d("3d", (41, 41, 21), 20.0, 8.0, 2.0, 20263)
+    s = 1.0 / W._velocity3d(g, 2.0)
+    T, cyc = O.eik_forward(g, s, g.index(10, 10, 0))
+    assert 0 < cyc < 100 and np.all(T >= 0) and np.isfinite(T).all()
