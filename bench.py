@@ -1,0 +1,397 @@
+"""Benchmark: paired J p + J^T y node-updates/s of the frozen full-metric tangent.
+
+Workload (3-D tomography-scale apply): 101 x 101 x 51 curvilinear grid over
+20 x 20 x 8 km, Gaussian-hill topography on a seeded smooth random surface,
+v = 2.0 + 0.5 z km/s with a +-5% 2 km checkerboard, 25 surface sources, a block of
+R = 64 model-space right-hand sides shared by all sources, 441 surface receivers.
+One step = the whole hot path once: J p (M, C, forward block traversal, P sampling)
+and J^T y (P^T, reverse traversal with U^T/L^T/P^T blocks, C^T M^T, sum over sources),
+FP32 substitution with FP64 SCC blocks.  Node-updates per step = 2 N S R.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own 25 sources (weak scaling); J^T's
+source sum ends in one NCCL all-reduce of g [N][R].
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "J·v+Jᵀ·w node-updates/s per B300 vs GPU sweeping; % HBM roofline"
+UNIT = "node-updates/s"
+WORKLOAD = "3d-101x101x51-S25-R64 (config: 3-D tomography-scale apply)"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region (read-only queries)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def algorithmic_bytes(st_list, R: int, esz: int, S: int, N: int, n_rec: int) -> dict:
+    """Bytes each call must move with this layout (per call, all sources):
+    structure per (source, node): perm 4 + row offset 4 + C*M 4 + receiver slot 4 and
+    edges x (index 4 + weight 4), read once per call and shared by the R right-hand
+    sides.  J p: read p for every node-update (each source's traversal reads it) and
+    write dT (downstream levels read it back) -> 2 x esz per node-update, plus d_rec.
+    J^T y: write lam for every node-update, read y, write g = sum_a C^T M^T lam_a once.
+    (The separate source-sum kernel re-reads lam; that re-read is not counted.)"""
+    edges = sum(s["edges"] for s in st_list)
+    struct = S * N * 16 + edges * 8
+    upd = S * N * R
+    fwd = upd * esz * 2 + struct + n_rec * S * R * esz
+    bwd = upd * esz + struct + n_rec * S * R * esz + N * R * esz
+    return {"fwd": fwd, "bwd": bwd, "struct_per_node": struct / (S * N), "updates": upd,
+            "fwd_per_update": fwd / upd, "bwd_per_update": bwd / upd}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2609_14982_b300 import eik
+    from paper_2609_14982_b300 import workloads as W
+    from paper_2609_14982_b300.sharding import reduce_model_gradient
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    wl = W.config3()
+    g = wl.grid
+    src = wl.src.copy()
+    if rank > 0:   # each rank owns its own 25 sources: shift the lattice by `rank` nodes in x
+        src = np.array([g.index(10 + 20 * (a // 5) + rank % 10, 10 + 20 * (a % 5), 0) for a in range(len(src))],
+                       dtype=np.int32)
+    if args.sources > 0:
+        src = src[:args.sources]
+    S, N, R, n_rec = len(src), g.N, wl.R, len(wl.rec)
+    workload = WORKLOAD if S == 25 else WORKLOAD.replace("S25", f"S{S}")
+    dg = eik.DeviceGrid(g, device=dev)
+    s = torch.tensor(wl.s, device=dev)
+    t0 = time.time()
+    cache = args.state_cache
+    if cache and os.path.exists(cache):
+        # states written by an earlier run of this command (profiling runs skip the state solve)
+        T = torch.tensor(np.load(cache), device=dev)
+        assert tuple(T.shape) == (S, N)
+        cyc = -1
+    else:
+        T, cyc = eik.eik_forward(dg, s, src)
+        if cache:
+            np.save(cache, T.cpu().numpy())
+    torch.cuda.synchronize()
+    t_state = time.time() - t0
+    opts = eik.default_opts(schedule=eik.SCHED_LEVELS if args.schedule == "levels" else eik.SCHED_PERSISTENT)
+    t0 = time.time()
+    tan = eik.Tangent(dg, T, s, src, rec=wl.rec, opts=opts)
+    torch.cuda.synchronize()
+    t_setup = time.time() - t0
+    st = [tan.stats(a) for a in range(S)]
+
+    dtype = torch.float32
+    gen = torch.Generator(dev).manual_seed(20263 + rank)
+    p = torch.randn((N, R), device=dev, dtype=dtype, generator=gen)
+    y = torch.randn((S, n_rec, R), device=dev, dtype=dtype, generator=gen)
+    d_rec = torch.empty((S, n_rec, R), device=dev, dtype=dtype)
+    gvec = torch.empty((N, R), device=dev, dtype=dtype)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        tan.apply(p, shared_model=True, d_rec=d_rec)
+        tan.apply_T(y, sum_sources=True, g=gvec)
+        reduce_model_gradient(gvec)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    tan.status()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk = Clocks(torch.cuda.current_device())
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    time.sleep(0.3)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for k in range(args.steps):
+        a, b, c = evs[k]
+        a.record(stream)
+        tan.apply(p, shared_model=True, d_rec=d_rec)
+        b.record(stream)
+        tan.apply_T(y, sum_sources=True, g=gvec)
+        c.record(stream)
+        reduce_model_gradient(gvec)
+    end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    tan.status()
+    ms = start.elapsed_time(end) / args.steps
+    t_fwd = [a.elapsed_time(b) for a, b, _ in evs]
+    t_bwd = [b.elapsed_time(c) for _, b, c in evs]
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt)
+    upd_step = 2.0 * N * S * R * world
+    value = upd_step / (ms / 1e3)
+
+    # ---- end to end through the public API: pinned host inputs in, results out
+    p_h = torch.empty((N, R), dtype=dtype, pin_memory=True).copy_(p.cpu())
+    y_h = torch.empty((S, n_rec, R), dtype=dtype, pin_memory=True).copy_(y.cpu())
+    drec_h = torch.empty((S, n_rec, R), dtype=dtype, pin_memory=True)
+    g_h = torch.empty((N, R), dtype=dtype, pin_memory=True)
+    p_d = torch.empty_like(p)
+    y_d = torch.empty_like(y)
+
+    def e2e_step():
+        p_d.copy_(p_h, non_blocking=True)
+        y_d.copy_(y_h, non_blocking=True)
+        tan.apply(p_d, shared_model=True, d_rec=d_rec)
+        tan.apply_T(y_d, sum_sources=True, g=gvec)
+        reduce_model_gradient(gvec)
+        drec_h.copy_(d_rec, non_blocking=True)
+        g_h.copy_(gvec, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt)
+    h2d = (p_h.numel() + y_h.numel()) * 4
+    d2h = (drec_h.numel() + g_h.numel()) * 4
+
+    if rank != 0:
+        tan.free()
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (forward or reverse traversal)
+    peak, peak_kind = _peaks()
+    ab = algorithmic_bytes(st, R, 4, S, N, n_rec)
+    mf, mb = statistics.mean(t_fwd), statistics.mean(t_bwd)
+    dom = "fwd" if mf >= mb else "bwd"
+    dom_ms = max(mf, mb)
+    achieved = ab[dom] / (dom_ms / 1e3) / 1e9
+    other = "bwd" if dom == "fwd" else "fwd"
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "k_traverse_persistent<float,4,%s>" % ("false" if dom == "fwd" else "true"),
+                "bytes_per_launch": ab[dom], "bytes_per_update": round(ab[dom + "_per_update"], 3),
+                "peak_kind": f"{peak_kind} hbm_gbs",
+                "other_direction": {"dir": other, "ms": round(min(mf, mb), 4),
+                                    "frac": round(ab[other] / (min(mf, mb) / 1e3) / 1e9 / peak, 4)}}
+
+    # ---- the plain form on the same B300: directional sweeping of the same operator
+    sweep = None
+    if not args.no_sweep:
+        Rs = 8
+        q = torch.randn((S, N, Rs), device=dev, dtype=dtype, generator=gen)
+        so = eik.default_opts(sweep_tol=1e-6)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        _, c1 = tan.sweep(q, transpose=False, opts=so)
+        _, c2 = tan.sweep(q, transpose=True, opts=so)
+        torch.cuda.synchronize()
+        ts = time.time() - t0
+        sweep = {"value": 2.0 * N * S * Rs / ts, "unit": UNIT, "cycles": [c1, c2], "R": Rs,
+                 "tol": 1e-6, "speedup_btf_over_sweep": round(value / (2.0 * N * S * Rs / ts), 1)}
+
+    cpu = None if args.no_cpu else cpu_baseline(wl, args.cpu_sample_sources)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64blocks",
+        "data": "synthetic (seeded recipe of the 3-D tomography-scale config; no public dataset)",
+        "config": {"workload": workload, "grid": list(g.n), "nodes": N, "sources_per_gpu": S, "rhs": R,
+                   "receivers": n_rec, "precision": "FP32 substitution, FP64 SCC blocks",
+                   "schedule": args.schedule, "l2": "inputs larger than L2 (dT/lam 3.3 GB per direction)",
+                   "parallelism": f"source-sharded x{world}" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": upd_step / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * (3 if args.schedule == "persistent" else (2 * max(x["levels"] for x in st) + 1)),
+        "clocks": clocks,
+        "sweep_baseline": sweep,
+        "setup": {"eik_forward_s": round(t_state, 3), "eik_cycles": cyc, "tangent_build_s": round(t_setup, 3),
+                  "levels_max": max(x["levels"] for x in st), "nontrivial_scc": sum(x["nontrivial"] for x in st),
+                  "largest_scc": max(x["largest"] for x in st), "edges_per_node": sum(x["edges"] for x in st) / (S * N)},
+        "kernel_ms": {"fwd": round(mf, 4), "bwd": round(mb, 4)},
+    }
+    print(json.dumps(out), flush=True)
+    tan.free()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(wl, n_src: int, R: int = 32) -> dict:
+    """The CPU oracle as it stands (single-threaded C, FP64 block traversal) on a bounded
+    sample of the workload: `n_src` sources (their states from the oracle's own state
+    solve), R right-hand sides each, one J and one J^T solve per right-hand side."""
+    import oracle as O
+    g = wl.grid
+    _, G, _ = O.metric(g)
+    rng = np.random.default_rng(7)
+    t_apply = 0.0
+    upd = 0
+    for a in range(n_src):
+        k = int(wl.src[(a * 7) % len(wl.src)])
+        T, _ = O.eik_forward(g, wl.s, k)
+        t = O.build_tangent(g, G, T, wl.s, k)
+        q = rng.standard_normal((g.N, R))
+        t0 = time.perf_counter()
+        for r in range(R):
+            O.solve(t, q[:, r])
+            O.solve_T(t, q[:, r])
+        t_apply += time.perf_counter() - t0
+        upd += 2 * g.N * R
+    return {"value": upd / t_apply, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_src} sources x {R} RHS of the full grid, J and J^T solves, FP64, {t_apply:.1f} s timed"}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle timed on the host, same metric and workload,
+    each step a bounded sample (one source, a few right-hand sides)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2609_14982_b300 import workloads as W
+    wl = W.config3()
+    g = wl.grid
+    _, G, _ = O.metric(g)
+    k = int(wl.src[12])
+    T, _ = O.eik_forward(g, wl.s, k)
+    t = O.build_tangent(g, G, T, wl.s, k)
+    rng = np.random.default_rng(3)
+    Rs = 8
+    q = rng.standard_normal((g.N, Rs))
+
+    def step():
+        for r in range(Rs):
+            O.solve(t, q[:, r])
+            O.solve_T(t, q[:, r])
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = 2 * g.N * Rs / dt
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample": f"1 source x {Rs} RHS per step"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"1 source x {Rs} RHS, J and J^T solves per step"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--schedule", choices=["persistent", "levels"], default="persistent")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample-sources", type=int, default=2)
+    ap.add_argument("--sources", type=int, default=0, help="use only the first K sources (small profiling case)")
+    ap.add_argument("--state-cache", default="", help="load/save the solved states (.npy) to skip the state solve")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

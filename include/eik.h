@@ -166,8 +166,8 @@ int tangent_apply(eik_tangent *t, const void *p, int shared_model, int R,
  *   y            device [S][n_rec][R]
  *   g            device [N][R] if sum_sources else [S][N][R]
  *   lam_full     device [S][N][R] or NULL (internal workspace)
- * The source sum is a deterministic reduction in source order (FP64 accumulation for
- * EIK_F32).
+ * The source sum is a deterministic reduction in source order (EIK_F64: FP64;
+ * EIK_F32: FP32 products with a compensated FP32 sum).
  */
 int tangent_apply_T(eik_tangent *t, const void *y, int R, int sum_sources,
                     void *g, void *lam_full, int dtype, eik_stream stream);
@@ -179,6 +179,12 @@ int tangent_apply_T(eik_tangent *t, const void *y, int R, int sum_sources,
  */
 int tangent_solve(eik_tangent *t, const void *q, int R, void *x, int dtype, eik_stream stream);
 int tangent_solve_T(eik_tangent *t, const void *r, int R, void *x, int dtype, eik_stream stream);
+
+/*
+ * tangent_sample -- receiver sampling P_a of a per-source field (Sec. 4.4, P_a):
+ * out[a][k] = field[a][rec_a[k]], field device [S][N] FP64, out device [S][n_rec] FP64.
+ */
+int tangent_sample(const eik_tangent *t, const double *field, double *out, eik_stream stream);
 
 /* Counts of one source's structure (Sec. 5.2, Eq. graph-fractions; Table 4 rows). Host. */
 int tangent_stats(const eik_tangent *t, int source, eik_stats *out);
@@ -231,6 +237,30 @@ void tangent_free(eik_tangent *t);
  */
 int sweep_apply(eik_tangent *t, int transpose, const void *b, int R, void *x, int dtype,
                 const eik_opts *opts, int *cycles, eik_stream stream);
+
+/*
+ * LSQR on the frozen Jacobian (Paige & Saunders 1982): the inner Krylov least-squares
+ * solve of Sec. 4.5 / Alg. 1 step 20 (without the regularization rows), min |J x - b|
+ * for a slowness-type model x [N] and data b [S][n_rec], using tangent_apply and
+ * tangent_apply_T (sum over sources) with one right-hand side.  All vectors and
+ * scalars stay on the device, so one iteration can be captured in a CUDA graph.
+ *   lsqr_create   allocates the work vectors (owned by the solver) for tangent t;
+ *                 dtype EIK_F64 or EIK_F32 (vectors and traversal precision)
+ *   lsqr_start    device b [S][n_rec]: beta u = b, alpha v = J^T u, w = v, x = 0
+ *   lsqr_iterate  runs `iters` iterations; use_graph != 0 captures one iteration into a
+ *                 CUDA graph on the first call (stream must not be the legacy default
+ *                 stream) and replays it
+ *   lsqr_solution copies x (device [N], may be NULL) and, if scalars != NULL, the host
+ *                 doubles {alpha, beta, rhobar, phibar, phi, rho, theta, c, s};
+ *                 phibar is the current residual norm |b - J x|
+ *   lsqr_free     releases the solver (not the tangent)
+ */
+typedef struct eik_lsqr eik_lsqr;
+int lsqr_create(eik_tangent *t, int dtype, eik_lsqr **out);
+int lsqr_start(eik_lsqr *l, const void *b, eik_stream stream);
+int lsqr_iterate(eik_lsqr *l, int iters, int use_graph, eik_stream stream);
+int lsqr_solution(eik_lsqr *l, void *x, double *scalars, eik_stream stream);
+void lsqr_free(eik_lsqr *l);
 
 #ifdef __cplusplus
 }

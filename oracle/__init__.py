@@ -359,3 +359,33 @@ def JT(tans, s, rec, y, model=MODEL_SLOWNESS, sum_sources=True, solver=solve_T):
         outs.append(m[:, None] * t.cs[:, None] * lam)
     outs = np.stack(outs)
     return outs.sum(axis=0) if sum_sources else outs
+
+
+# --------------------------------------------------------------------------- LSQR
+def lsqr(apply_J, apply_JT, b: np.ndarray, iters: int):
+    """LSQR (Paige and Saunders, 1982), plain numpy, x0 = 0, no damping: the Krylov
+    least-squares loop that Sec. 4.5 runs on the paired actions.  Returns (x, phibar)."""
+    beta = np.linalg.norm(b)
+    u = b / beta
+    v = apply_JT(u)
+    alpha = np.linalg.norm(v)
+    v = v / alpha
+    w = v.copy()
+    x = np.zeros_like(v)
+    phibar, rhobar = beta, alpha
+    for _ in range(iters):
+        u = apply_J(v) - alpha * u
+        beta = np.linalg.norm(u)
+        u = u / beta
+        v = apply_JT(u) - beta * v
+        alpha = np.linalg.norm(v)
+        v = v / alpha
+        rho = np.hypot(rhobar, beta)
+        c, s = rhobar / rho, beta / rho
+        theta = s * alpha
+        rhobar = -c * alpha
+        phi = c * phibar
+        phibar = s * phibar
+        x = x + (phi / rho) * w
+        w = v - (theta / rho) * w
+    return x, phibar

@@ -111,6 +111,19 @@ int tangent_solve_T(eik_tangent *t, const void *r, int R, void *x, int dtype, ei
     })
 }
 
+int tangent_sample(const eik_tangent *tt, const double *field, double *out, eik_stream stream)
+{
+    EIK_GUARD({
+        if (!tt || !field || !out) { eik::set_error("bad tangent_sample arguments"); return EIK_ERR_INVALID; }
+        Tangent *t = tt->impl;
+        long long n = (long long)t->S * t->n_rec;
+        if (n == 0) return EIK_OK;
+        eik::launch_sample(t->N, t->S, t->n_rec, t->rec_nat, field, out, (cudaStream_t)stream);
+        EIK_CHECK_LAUNCH();
+        return EIK_OK;
+    })
+}
+
 int tangent_stats(const eik_tangent *t, int source, eik_stats *out)
 {
     if (!t || !out || source < 0 || source >= t->impl->S) { eik::set_error("bad tangent_stats arguments"); return EIK_ERR_INVALID; }

@@ -94,6 +94,7 @@ struct TravParams {
     void *x;               // dT or lam [S][N][R]
     void *aux;             // forward: d_rec [S][n_rec][R]; transpose (no sum): g [S][N][R]
     const int4 *items;
+    const int2 *ebeg;      // per item: staged edge range
     const int *item_cnt;   // [S][maxL] items per (source, step) of this direction
     int *done;             // [S][maxL]
     int *ticket;
@@ -107,70 +108,139 @@ struct TravParams {
 };
 
 // ---------------------------------------------------------------- singleton items
-// Each group of G lanes owns one node at a time; lane l handles right-hand sides
-// l*V .. l*V+V-1, then strides by G*V.
+// The structure of one item (at most ITEM_MAX positions of one level of one source and
+// their rows) is staged into shared memory by all threads in one round of independent
+// loads; afterwards a node costs only its own vector loads (input, upstream values),
+// all issued before they are summed.
+constexpr int MAX_ROW = 6;   // at most 2 * ndim faces per row
+
+template <typename T> struct Stage {
+    int perm[ITEM_MAX];
+    int rec[ITEM_MAX];
+    int rp[ITEM_MAX + 1];
+    T cq[ITEM_MAX];
+    int en[MAX_ROW * ITEM_MAX];
+    T ew[MAX_ROW * ITEM_MAX];
+};
+
+template <typename T>
+__device__ __forceinline__ void stage_item(const TravParams &P, Stage<T> &sm, int a, int p0, int p1, int2 eb)
+{
+    const long long N = P.N;
+    const int np = p1 - p0, ne = eb.y - eb.x;
+    const int *perm = P.perm + a * N + p0;
+    const int *rp = P.rowptr + a * (N + 1) + p0;
+    const T *cq = reinterpret_cast<const T *>(P.cq) + a * N + p0;
+    const int *rs = P.rec_slot + a * N + p0;
+    const long long eb0 = P.ebase[a] + eb.x;
+    const int *en = P.enode + eb0;
+    const T *ew = reinterpret_cast<const T *>(P.ew) + eb0;
+    for (int k = threadIdx.x; k <= np; k += blockDim.x) {
+        sm.rp[k] = __ldg(rp + k) - eb.x;
+        if (k < np) {
+            sm.perm[k] = __ldg(perm + k);
+            sm.rec[k] = __ldg(rs + k);
+            sm.cq[k] = __ldg(cq + k);
+        }
+    }
+    for (int k = threadIdx.x; k < ne; k += blockDim.x) {
+        sm.en[k] = __ldg(en + k);
+        sm.ew[k] = __ldg(ew + k);
+    }
+}
+
+// Each group of G lanes owns up to two nodes of the item (slot and slot + nslot); lane l
+// handles right-hand sides l*V .. l*V+V-1, then strides by G*V.  All loads of both
+// nodes (input and up to MAX_ROW upstream values each) are issued before any sum.
 template <typename T, int V, bool TR>
-__device__ __forceinline__ void run_singletons(const TravParams &P, int a, int p0, int p1, int G)
+__device__ __forceinline__ Pack<T, V> node_input(const TravParams &P, int a, int v, int rec, T c, int r)
+{
+    const long long N = P.N;
+    const int R = P.R;
+    const T *in = reinterpret_cast<const T *>(P.in);
+    Pack<T, V> acc;
+    if (!TR) {
+        if (P.mode == MODE_J) {
+            Pack<T, V> q = load_ro<T, V>(in + ((P.shared_in ? 0 : (long long)a * N) + v) * R + r);
+#pragma unroll
+            for (int u = 0; u < V; ++u) acc.v[u] = c * q.v[u];
+        } else {
+            acc = load_ro<T, V>(in + ((long long)a * N + v) * R + r);
+        }
+    } else {
+        if (P.mode == MODE_J) {
+            if (rec >= 0) acc = load_ro<T, V>(in + ((long long)a * P.n_rec + rec) * R + r);
+            else {
+#pragma unroll
+                for (int u = 0; u < V; ++u) acc.v[u] = T(0);
+            }
+        } else {
+            acc = load_ro<T, V>(in + ((long long)a * N + v) * R + r);
+        }
+    }
+    return acc;
+}
+
+template <typename T, int V, bool TR>
+__device__ __forceinline__ void node_output(const TravParams &P, int a, int v, int rec, T c, int r, T *x,
+                                            const Pack<T, V> &acc)
+{
+    const long long N = P.N;
+    const int R = P.R;
+    T *aux = reinterpret_cast<T *>(P.aux);
+    store<T, V>(x + (long long)v * R + r, acc);
+    if (P.mode == MODE_J && aux) {
+        if (!TR) {
+            if (rec >= 0) store<T, V>(aux + ((long long)a * P.n_rec + rec) * R + r, acc);
+        } else if (!P.sum) {
+            Pack<T, V> gv;
+#pragma unroll
+            for (int u = 0; u < V; ++u) gv.v[u] = c * acc.v[u];
+            store<T, V>(aux + ((long long)a * N + v) * R + r, gv);
+        }
+    }
+}
+
+template <typename T, int V, bool TR>
+__device__ __forceinline__ void run_singletons(const TravParams &P, const Stage<T> &sm, int a, int np, int G)
 {
     const int lane = threadIdx.x % G, slot = threadIdx.x / G, nslot = blockDim.x / G;
     const long long N = P.N;
     const int R = P.R;
-    const int *perm = P.perm + a * N;
-    const int *rp = P.rowptr + a * (N + 1);
-    const long long eb = P.ebase[a];
-    const int *en = P.enode + eb;
-    const T *ew = reinterpret_cast<const T *>(P.ew) + eb;
-    const T *cq = reinterpret_cast<const T *>(P.cq) + a * N;
-    const int *rs = P.rec_slot + a * N;
-    const T *in = reinterpret_cast<const T *>(P.in);
     T *x = reinterpret_cast<T *>(P.x) + a * N * R;
-    T *aux = reinterpret_cast<T *>(P.aux);
-    for (int p = p0 + slot; p < p1; p += nslot) {
-        const int v = __ldg(perm + p);
-        if (v < 0) continue;                      // member of a nontrivial block
-        const int e0 = __ldg(rp + p), e1 = __ldg(rp + p + 1);
-        const int rec = __ldg(rs + p);
-        const T c = __ldg(cq + p);
+    for (int k0 = slot; k0 < np; k0 += 2 * nslot) {
+        const int k1 = k0 + nslot;
+        const bool has1 = k1 < np;
+        const int v0 = sm.perm[k0], v1 = has1 ? sm.perm[k1] : -1;
+        const bool on0 = v0 >= 0, on1 = v1 >= 0;  // members of nontrivial blocks are skipped
+        const int e00 = sm.rp[k0], c0 = on0 ? sm.rp[k0 + 1] - e00 : 0;
+        const int e01 = has1 ? sm.rp[k1] : 0, c1 = on1 ? sm.rp[k1 + 1] - e01 : 0;
+        const int rec0 = sm.rec[k0], rec1 = has1 ? sm.rec[k1] : -1;
+        const T cq0 = sm.cq[k0], cq1 = has1 ? sm.cq[k1] : T(0);
         for (int r = lane * V; r < R; r += G * V) {
-            Pack<T, V> acc;
-            if (!TR) {
-                if (P.mode == MODE_J) {
-                    const T *src = in + ((P.shared_in ? 0 : (long long)a * N) + v) * R + r;
-                    Pack<T, V> q = load_ro<T, V>(src);
+            Pack<T, V> a0, a1, x0[MAX_ROW], x1[MAX_ROW];
+            if (on0) a0 = node_input<T, V, TR>(P, a, v0, rec0, cq0, r);
+            if (on1) a1 = node_input<T, V, TR>(P, a, v1, rec1, cq1, r);
 #pragma unroll
-                    for (int k = 0; k < V; ++k) acc.v[k] = c * q.v[k];
-                } else {
-                    acc = load_ro<T, V>(in + ((long long)a * N + v) * R + r);
-                }
-            } else {
-                if (P.mode == MODE_J) {
-                    if (rec >= 0) acc = load_ro<T, V>(in + ((long long)a * P.n_rec + rec) * R + r);
-                    else {
-#pragma unroll
-                        for (int k = 0; k < V; ++k) acc.v[k] = T(0);
-                    }
-                } else {
-                    acc = load_ro<T, V>(in + ((long long)a * N + v) * R + r);
-                }
+            for (int e = 0; e < MAX_ROW; ++e) {
+                if (e < c0) x0[e] = load_l2<T, V>(x + (long long)sm.en[e00 + e] * R + r);
+                if (e < c1) x1[e] = load_l2<T, V>(x + (long long)sm.en[e01 + e] * R + r);
             }
-            for (int e = e0; e < e1; ++e) {
-                const int j = __ldg(en + e);
-                const T w = __ldg(ew + e);
-                Pack<T, V> xj = load_l2<T, V>(x + (long long)j * R + r);
 #pragma unroll
-                for (int k = 0; k < V; ++k) acc.v[k] += w * xj.v[k];
-            }
-            store<T, V>(x + (long long)v * R + r, acc);
-            if (P.mode == MODE_J && aux) {
-                if (!TR) {
-                    if (rec >= 0) store<T, V>(aux + ((long long)a * P.n_rec + rec) * R + r, acc);
-                } else if (!P.sum) {
-                    Pack<T, V> gv;
+            for (int e = 0; e < MAX_ROW; ++e) {
+                if (e < c0) {
+                    const T w = sm.ew[e00 + e];
 #pragma unroll
-                    for (int k = 0; k < V; ++k) gv.v[k] = c * acc.v[k];
-                    store<T, V>(aux + ((long long)a * N + v) * R + r, gv);
+                    for (int u = 0; u < V; ++u) a0.v[u] += w * x0[e].v[u];
+                }
+                if (e < c1) {
+                    const T w = sm.ew[e01 + e];
+#pragma unroll
+                    for (int u = 0; u < V; ++u) a1.v[u] += w * x1[e].v[u];
                 }
             }
+            if (on0) node_output<T, V, TR>(P, a, v0, rec0, cq0, r, x, a0);
+            if (on1) node_output<T, V, TR>(P, a, v1, rec1, cq1, r, x, a1);
         }
     }
 }
@@ -270,18 +340,25 @@ __device__ void run_block(const TravParams &P, int a, int b)
 }
 
 template <typename T, int V, bool TR>
-__device__ __forceinline__ void run_item(const TravParams &P, int4 it, int G)
+__device__ __forceinline__ void run_item(const TravParams &P, Stage<T> &sm, int4 it, int2 eb, int G)
 {
-    if (it.z >= 0) run_singletons<T, V, TR>(P, it.x, it.z, it.w, G);
-    else run_block<T, TR>(P, it.x, ~it.z);
+    if (it.z >= 0) {
+        stage_item<T>(P, sm, it.x, it.z, it.w, eb);
+        __syncthreads();
+        run_singletons<T, V, TR>(P, sm, it.x, it.w - it.z, G);
+    } else {
+        run_block<T, TR>(P, it.x, ~it.z);
+    }
 }
 
 // ---------------------------------------------------------------- persistent schedule
 template <typename T, int V, bool TR>
 __global__ void __launch_bounds__(256) k_traverse_persistent(TravParams P, int G)
 {
+    __shared__ Stage<T> sm;
     __shared__ int s_item;
     __shared__ int s_ok;
+    __shared__ int2 s_eb;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(P.ticket, 1);
         __syncthreads();
@@ -289,6 +366,7 @@ __global__ void __launch_bounds__(256) k_traverse_persistent(TravParams P, int G
         if (i >= P.nitems) break;
         const int4 it = P.items[i];
         if (threadIdx.x == 0) {
+            s_eb = P.ebeg[i];
             int ok = 1;
             if (it.y > 0) {
                 const int *flag = P.done + (long long)it.x * P.maxL + it.y - 1;
@@ -308,7 +386,7 @@ __global__ void __launch_bounds__(256) k_traverse_persistent(TravParams P, int G
         }
         __syncthreads();
         if (!s_ok) break;
-        run_item<T, V, TR>(P, it, G);
+        run_item<T, V, TR>(P, sm, it, s_eb, G);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -321,21 +399,58 @@ __global__ void __launch_bounds__(256) k_traverse_persistent(TravParams P, int G
 template <typename T, int V, bool TR>
 __global__ void __launch_bounds__(256) k_traverse_step(TravParams P, int G, int first)
 {
-    run_item<T, V, TR>(P, P.items[first + blockIdx.x], G);
+    __shared__ Stage<T> sm;
+    run_item<T, V, TR>(P, sm, P.items[first + blockIdx.x], P.ebeg[first + blockIdx.x], G);
 }
 
-// g[j][r] = sum_a cq_a[j] lam_a[j][r], in source order (FP64 accumulation)
+// g[j][r] = sum_a cq_a[j] lam_a[j][r] in source order.  FP64 path: FP64 products and
+// sum.  FP32 path: FP32 products with a compensated (Kahan) FP32 sum, so the rounding
+// error does not grow with the number of sources (B300's FP64 rate would make an FP64
+// accumulation the bottleneck of this pass).  Loads are issued SUMB at a time.
+constexpr int SUMB = 8;
+
 template <typename T>
 __global__ void k_source_sum(long long N, int S, int R, const T *__restrict__ cqn, const T *__restrict__ lam,
-                             const double *__restrict__ cqn64, T *__restrict__ g)
+                             T *__restrict__ g)
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= N * R) return;
     long long j = idx / R;
-    double acc = 0.0;
-    for (int a = 0; a < S; ++a) acc += cqn64[(long long)a * N + j] * (double)lam[(long long)a * N * R + idx];
-    g[idx] = (T)acc;
-    (void)cqn;
+    T acc = 0, comp = 0;
+    for (int a0 = 0; a0 < S; a0 += SUMB) {
+        T vals[SUMB];
+#pragma unroll
+        for (int b = 0; b < SUMB; ++b)
+            vals[b] = a0 + b < S ? __ldg(cqn + (long long)(a0 + b) * N + j) * __ldcs(lam + (long long)(a0 + b) * N * R + idx) : T(0);
+#pragma unroll
+        for (int b = 0; b < SUMB; ++b) {
+            if (sizeof(T) == 8) {
+                acc += vals[b];
+            } else {
+                T y = vals[b] - comp;
+                T t = acc + y;
+                comp = (t - acc) - y;
+                acc = t;
+            }
+        }
+    }
+    g[idx] = acc;
+}
+
+// receiver sampling P: out[a][k] = field[a][rec[a][k]]
+__global__ void k_sample(long long N, int S, int n_rec, const int *__restrict__ rec, const double *__restrict__ field,
+                         double *__restrict__ out)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)S * n_rec) return;
+    long long a = i / n_rec;
+    out[i] = field[a * N + rec[i]];
+}
+
+void launch_sample(long long N, int S, int n_rec, const int *rec, const double *field, double *out, cudaStream_t st)
+{
+    long long n = (long long)S * n_rec;
+    k_sample<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(N, S, n_rec, rec, field, out);
 }
 
 // ---------------------------------------------------------------- host side
@@ -361,7 +476,8 @@ int ensure_workspace(Tangent *t, size_t vec_bytes, size_t blk_elems)
 template <typename T, int V, bool TR>
 static int launch_traverse(Tangent *t, TravParams &P, int G, cudaStream_t st)
 {
-    const int threads = 256;
+    // a CTA holds ITEM_MAX / 2 node slots of G lanes (two nodes per slot), at most 256 threads
+    const int threads = std::min(256, std::max(32, ITEM_MAX * G / 2));
     if (t->opts.schedule == EIK_SCHED_LEVELS) {
         const std::vector<int> &sp = TR ? t->step_ptr_bwd : t->step_ptr_fwd;
         for (int s = 0; s < t->maxL; ++s) {
@@ -437,6 +553,7 @@ int traverse(Tangent *t, bool TR, int mode, const void *in, int shared_in, int R
     P.rec_slot = t->rec_slot;
     P.in = in; P.x = x; P.aux = out_aux;
     P.items = TR ? t->items_bwd : t->items_fwd;
+    P.ebeg = TR ? t->ebeg_bwd : t->ebeg_fwd;
     P.item_cnt = t->item_cnt + (TR ? (size_t)t->S * t->maxL : 0);
     P.done = t->done; P.ticket = t->ticket; P.err = t->err;
     P.blk_desc = t->blk_desc; P.blk_off = t->blk_off; P.lu = t->lu; P.piv = t->piv; P.ws = t->ws_blk;
@@ -451,9 +568,9 @@ int traverse(Tangent *t, bool TR, int mode, const void *in, int shared_in, int R
         long long n = t->N * R;
         unsigned blocks = (unsigned)((n + 255) / 256);
         if (dtype == EIK_F32)
-            k_source_sum<float><<<blocks, 256, 0, st>>>(t->N, t->S, R, t->cqn32, (const float *)x, t->cqn64, (float *)out_aux);
+            k_source_sum<float><<<blocks, 256, 0, st>>>(t->N, t->S, R, t->cqn32, (const float *)x, (float *)out_aux);
         else
-            k_source_sum<double><<<blocks, 256, 0, st>>>(t->N, t->S, R, t->cqn64, (const double *)x, t->cqn64, (double *)out_aux);
+            k_source_sum<double><<<blocks, 256, 0, st>>>(t->N, t->S, R, t->cqn64, (const double *)x, (double *)out_aux);
         EIK_CHECK_LAUNCH();
     }
     return EIK_OK;

@@ -22,6 +22,9 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
 
 #define EIK_CHECK_LAUNCH() EIK_CHECK(cudaGetLastError())
 
+// Largest singleton range of one work item (positions staged in shared memory).
+constexpr int ITEM_MAX = 32;
+
 // Device-side fault codes latched in Tangent::err (first one wins).
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_SINGULAR = 2, DEV_BAD_INDEX = 3 };
 
@@ -101,6 +104,8 @@ struct Tangent {
     int nitems = 0;
     int4 *items_fwd = nullptr;
     int4 *items_bwd = nullptr;
+    int2 *ebeg_fwd = nullptr;     // per item: [first, last) local edge offsets of its rows
+    int2 *ebeg_bwd = nullptr;
     std::vector<int> step_ptr_fwd, step_ptr_bwd;   // [maxL+1] items per step (host)
     int *item_cnt = nullptr;      // [S][maxL] items per (source, level); bwd uses reversed step
     int *done = nullptr;          // [S][maxL] completed items per (source, step)
@@ -129,5 +134,7 @@ int sweep(Tangent *t, bool transpose, const void *b, int R, void *x, int dtype,
           const eik_opts *opts, int *cycles, cudaStream_t stream);
 
 int ensure_workspace(Tangent *t, size_t vec_bytes, size_t blk_elems);
+
+void launch_sample(long long N, int S, int n_rec, const int *rec, const double *field, double *out, cudaStream_t st);
 
 }  // namespace eik

@@ -672,6 +672,16 @@ __global__ void k_local_labels(long long SN, long long N, int *label)
 }
 
 
+__global__ void k_item_edges(int n, long long N, const int4 *items, const int *rowptr, int2 *eb)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int4 it = items[i];
+    if (it.z < 0) { eb[i] = make_int2(0, 0); return; }
+    const int *rp = rowptr + (long long)it.x * (N + 1);
+    eb[i] = make_int2(rp[it.z], rp[it.w]);
+}
+
 __global__ void k_compact_heads(long long SN, const int *head, const int *scan, int *hpos)
 {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -719,7 +729,7 @@ void free_tangent(Tangent *t)
     void *ptrs[] = {t->perm, t->pos, t->label, t->level, t->rowptr, t->up_node, t->up_w32, t->up_w64, t->cptr,
                     t->dn_node, t->dn_w32, t->dn_w64, t->cq64, t->cq32, t->cqn64, t->cqn32, t->rec_slot,
                     t->rec_nat, t->nrow_cnt, t->nrow_node, t->nrow_w, t->cs_nat, t->blk_desc, t->blk_off, t->lu,
-                    t->piv, t->items_fwd, t->items_bwd, t->item_cnt, t->done, t->ticket, t->err, t->ws_vec,
+                    t->piv, t->items_fwd, t->items_bwd, t->ebeg_fwd, t->ebeg_bwd, t->item_cnt, t->done, t->ticket, t->err, t->ws_vec,
                     t->ws_blk, t->ebase_d, t->tbase_d};
     for (void *p : ptrs) if (p) cudaFree(p);
     delete t;
@@ -1055,7 +1065,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
 
     // ---- traversal work items: level-major over sources
     {
-        int chunk = opts->chunk > 0 ? opts->chunk : 64;
+        int chunk = opts->chunk > 0 ? std::min(opts->chunk, ITEM_MAX) : ITEM_MAX;
         std::vector<std::vector<int4>> per((size_t)S * maxL);
         std::vector<int> blk_ptr(S + 1, 0);
         // blocks are ordered by (source, position), hence by (source, level)
@@ -1099,6 +1109,11 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
         TRY(cudaMemcpyAsync(t->items_fwd, fw.data(), fw.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
         TRY(cudaMemcpyAsync(t->items_bwd, bw.data(), bw.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
         TRY(cudaMemcpyAsync(t->item_cnt, icnt.data(), icnt.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        TRY(dalloc(&t->ebeg_fwd, fw.size()));
+        TRY(dalloc(&t->ebeg_bwd, bw.size()));
+        k_item_edges<<<blocks_for((long long)fw.size()), 256, 0, st>>>((int)fw.size(), N, t->items_fwd, t->rowptr, t->ebeg_fwd);
+        k_item_edges<<<blocks_for((long long)bw.size()), 256, 0, st>>>((int)bw.size(), N, t->items_bwd, t->cptr, t->ebeg_bwd);
+        TRY(cudaGetLastError());
     }
 
     // ---- statistics

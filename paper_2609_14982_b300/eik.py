@@ -22,8 +22,9 @@ STATUS = {0: "OK", -1: "INVALID", -2: "OOM", -3: "SINGULAR_BLOCK", -4: "NOT_CONV
           -6: "CUDA", -7: "CYCLE"}
 
 EXPORTED = ["eik_opts_default", "eik_last_error", "eik_version", "eik_forward", "tangent_build", "tangent_apply",
-            "tangent_apply_T", "tangent_solve", "tangent_solve_T", "tangent_stats", "tangent_dims",
-            "tangent_export", "tangent_status", "tangent_free", "sweep_apply", "tangent_debug_hold"]
+            "tangent_apply_T", "tangent_solve", "tangent_solve_T", "tangent_sample", "tangent_stats", "tangent_dims",
+            "tangent_export", "tangent_status", "tangent_free", "sweep_apply", "tangent_debug_hold",
+            "lsqr_create", "lsqr_start", "lsqr_iterate", "lsqr_solution", "lsqr_free"]
 
 
 class EikError(RuntimeError):
@@ -71,6 +72,7 @@ def lib():
         L.tangent_apply_T.argtypes = [P, P, I, I, P, P, I, P]
         L.tangent_solve.argtypes = [P, P, I, P, I, P]
         L.tangent_solve_T.argtypes = [P, P, I, P, I, P]
+        L.tangent_sample.argtypes = [P, P, P, P]
         L.tangent_stats.argtypes = [P, I, C.POINTER(Stats)]
         L.tangent_dims.argtypes = [P, C.POINTER(I), C.POINTER(C.c_int64), C.POINTER(I)]
         L.tangent_export.argtypes = [P, I, P, P, P, P, P, P, P, P]
@@ -78,6 +80,12 @@ def lib():
         L.tangent_free.argtypes = [P]
         L.tangent_free.restype = None
         L.tangent_debug_hold.argtypes = [P, I, I]
+        L.lsqr_create.argtypes = [P, I, C.POINTER(P)]
+        L.lsqr_start.argtypes = [P, P, P]
+        L.lsqr_iterate.argtypes = [P, I, I, P]
+        L.lsqr_solution.argtypes = [P, P, P, P]
+        L.lsqr_free.argtypes = [P]
+        L.lsqr_free.restype = None
         L.sweep_apply.argtypes = [P, I, P, I, P, I, C.POINTER(Opts), C.POINTER(I), P]
         _lib = L
     return _lib
@@ -216,6 +224,13 @@ class Tangent:
                                      _stream()))
         return out
 
+    def sample(self, field: torch.Tensor, out=None):
+        """P_a: values of a per-source FP64 field [S, N] at each source's receivers."""
+        out = torch.empty((self.S, self.n_rec), dtype=torch.float64, device=field.device) if out is None else out
+        _check(lib().tangent_sample(self.h, _dev(field, torch.float64, "field"), _dev(out, torch.float64, "out"),
+                                    _stream()))
+        return out
+
     def sweep(self, b: torch.Tensor, transpose=False, opts: Opts | None = None, out=None):
         """Directional Gauss-Seidel sweeping of the same operator; returns (x, cycles)."""
         out = torch.empty_like(b) if out is None else out
@@ -253,3 +268,35 @@ class Tangent:
         _check(lib().tangent_export(self.h, a, *ptrs))
         return dict(label=label, level=level, perm=perm, level_ptr=level_ptr, row_ptr=row_ptr,
                     col=col[:st["edges"]], w=w[:st["edges"]], cs=cs, stats=st)
+
+
+class LSQR:
+    """Device LSQR on J of a tangent (one right-hand side, slowness-type model)."""
+
+    def __init__(self, tan: Tangent, dtype=torch.float64):
+        self.tan = tan
+        self.dtype = dtype
+        h = C.c_void_p()
+        _check(lib().lsqr_create(tan.h, _dt(dtype), C.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().lsqr_free(self.h)
+            self.h = C.c_void_p()
+
+    def start(self, b: torch.Tensor):
+        _check(lib().lsqr_start(self.h, _dev(b, self.dtype, "b"), _stream()))
+
+    def iterate(self, iters: int, use_graph: bool = True):
+        _check(lib().lsqr_iterate(self.h, iters, int(use_graph), _stream()))
+
+    def solution(self):
+        x = torch.empty(self.tan.N, dtype=self.dtype, device="cuda")
+        sc = (C.c_double * 9)()
+        _check(lib().lsqr_solution(self.h, _dev(x, self.dtype, "x"), sc, _stream()))
+        names = ("alpha", "beta", "rhobar", "phibar", "phi", "rho", "theta", "c", "s")
+        return x, dict(zip(names, list(sc)))
