@@ -307,6 +307,62 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_lsqr(args):
+    """Config 4: 201 x 201 x 101 grid, 64 sources, 2500 receivers, one right-hand side;
+    20 LSQR iterations on J with every iteration replayed from a CUDA graph.  Prints one
+    JSON line (paired node-updates/s of the Krylov loop, setup times)."""
+    import torch
+
+    from paper_2609_14982_b300 import eik
+    from paper_2609_14982_b300 import workloads as W
+    torch.cuda.set_device(0)
+    wl = W.config4()
+    g = wl.grid
+    src = wl.src if args.sources <= 0 else wl.src[:args.sources]
+    S, N = len(src), g.N
+    dg = eik.DeviceGrid(g)
+    s = torch.tensor(wl.s, device="cuda")
+    t0 = time.time()
+    T, cyc = eik.eik_forward(dg, s, src)
+    torch.cuda.synchronize()
+    t_state = time.time() - t0
+    t0 = time.time()
+    tan = eik.Tangent(dg, T, s, src, rec=wl.rec)
+    torch.cuda.synchronize()
+    t_setup = time.time() - t0
+    del T
+    st = [tan.stats(a) for a in range(S)]
+    dtype = torch.float64 if args.lsqr_dtype == "f64" else torch.float32
+    b = torch.randn((S, len(wl.rec)), device="cuda", dtype=dtype, generator=torch.Generator("cuda").manual_seed(20264))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        L = eik.LSQR(tan, dtype=dtype)
+        L.start(b)
+        L.iterate(1, use_graph=True)           # capture + first replay
+        L.start(b)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.iterate(20, use_graph=True)
+        e1.record(stream)
+        stream.synchronize()
+        x, sc = L.solution()
+    tan.status()
+    ms = e0.elapsed_time(e1) / 20
+    upd = 2.0 * N * S
+    out = {"metric": METRIC, "value": upd / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": 20, "warmup": 1,
+           "ms_per_step": ms, "higher_is_better": True, "dtype": args.lsqr_dtype,
+           "config": {"workload": f"3d-201x201x101-S{S}-lsqr20 (config: Gauss-Newton inner solve)", "nodes": N,
+                      "sources": S, "receivers": len(wl.rec), "step": "one LSQR iteration (J v, J^T u, vector ops), CUDA graph"},
+           "lsqr": {"phibar": sc["phibar"], "iterations": 20},
+           "setup": {"eik_forward_s": round(t_state, 2), "eik_cycles": cyc, "tangent_build_s": round(t_setup, 2),
+                     "levels_max": max(x["levels"] for x in st), "nontrivial_scc": sum(x["nontrivial"] for x in st),
+                     "largest_scc": max(x["largest"] for x in st)}}
+    print(json.dumps(out), flush=True)
+    L.free()
+    tan.free()
+
+
 def cpu_baseline(wl, n_src: int, R: int = 32) -> dict:
     """The CPU oracle as it stands (single-threaded C, FP64 block traversal) on a bounded
     sample of the workload: `n_src` sources (their states from the oracle's own state
@@ -384,11 +440,16 @@ def main():
     ap.add_argument("--cpu-sample-sources", type=int, default=2)
     ap.add_argument("--sources", type=int, default=0, help="use only the first K sources (small profiling case)")
     ap.add_argument("--state-cache", default="", help="load/save the solved states (.npy) to skip the state solve")
+    ap.add_argument("--workload", choices=["apply", "lsqr"], default="apply",
+                    help="apply: the benchmark line (3-D apply config); lsqr: the 20-iteration Krylov config")
+    ap.add_argument("--lsqr-dtype", choices=["f64", "f32"], default="f64")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "lsqr":
+        run_lsqr(args)
     else:
         run_ours(args)
 

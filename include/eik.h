@@ -81,6 +81,9 @@ typedef struct {
     /* sweeping baseline */
     double sweep_tol;          /* max |dx| <= sweep_tol * max |x| over one cycle (default 1e-12) */
     int sweep_max_cycles;      /* (default 10000) */
+    /* traversal */
+    int rhs_chunk;             /* process right-hand sides in column chunks of this many
+                                  (0 = all at once); bounds the internal workspace */
 } eik_opts;
 
 typedef struct {
@@ -212,6 +215,13 @@ int tangent_export(const eik_tangent *t, int source, int *label, int *level, int
  * that ran out), then clears it.
  */
 int tangent_status(eik_tangent *t, eik_stream stream);
+
+/*
+ * tangent_tune -- replace the run-time options of a built tangent: schedule, ctas_per_sm,
+ * rhs_chunk and wait_timeout_s are taken from opts (structure options are ignored).
+ * Used by the autotuner; affects later calls only.
+ */
+int tangent_tune(eik_tangent *t, const eik_opts *opts);
 
 /*
  * tangent_debug_hold -- test hook for the bounded device-side waits of the persistent

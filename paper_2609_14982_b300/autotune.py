@@ -1,0 +1,91 @@
+"""Autotuner for the traversal launch settings of a built tangent.
+
+The structure of a tangent is fixed at build time; how it is traversed is not.  This
+module times one J p and one J^T y (CUDA events on the current stream) for each
+candidate run-time setting -- schedule (persistent level queue or graph-replayed
+per-level launches), right-hand-side chunk, persistent CTAs per SM -- applies the
+fastest with tangent_tune and caches the choice per (grid size, sources, levels, R,
+dtype) in a JSON file.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import torch
+
+from . import eik
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "eik_autotune.json")
+
+
+def _key(tan, R: int, dtype) -> str:
+    st = tan.stats(0)
+    lv = max(tan.stats(a)["levels"] for a in range(tan.S))
+    return f"N{tan.N}-S{tan.S}-L{lv}-R{R}-{str(dtype).split('.')[-1]}-E{st['edges']}"
+
+
+def candidates(R: int, dtype) -> list:
+    unit = 4 if dtype == torch.float32 else 2
+    chunks = [0] + [c for c in (R // 2, R // 4) if c >= unit and c % unit == 0 and c < R]
+    out = []
+    for ch in chunks:
+        out.append({"schedule": eik.SCHED_LEVELS, "ctas_per_sm": 0, "rhs_chunk": ch})
+        for per_sm in (0, 1, 2):
+            out.append({"schedule": eik.SCHED_PERSISTENT, "ctas_per_sm": per_sm, "rhs_chunk": ch})
+    return out
+
+
+def time_setting(tan, p, y, reps: int = 3) -> float:
+    """Mean milliseconds of one J p + J^T y pair (after one untimed call)."""
+    tan.apply(p, shared_model=True)
+    tan.apply_T(y, sum_sources=True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        tan.apply(p, shared_model=True)
+        tan.apply_T(y, sum_sources=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tan.status()
+    return e0.elapsed_time(e1) / reps
+
+
+def autotune(tan, R: int, dtype=torch.float32, reps: int = 3, cache_path: str | None = DEFAULT_CACHE,
+             cands: list | None = None, seed: int = 0) -> dict:
+    """Pick the fastest setting for this tangent and R, apply it, return the record."""
+    key = _key(tan, R, dtype)
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        try:
+            with open(cache_path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    if key in cache and cands is None:
+        best = cache[key]["setting"]
+        tan.tune(**best)
+        return dict(cache[key], cached=True)
+    gen = torch.Generator("cuda").manual_seed(seed)
+    p = torch.randn((tan.N, R), device="cuda", dtype=dtype, generator=gen)
+    y = torch.randn((tan.S, max(tan.n_rec, 1), R), device="cuda", dtype=dtype, generator=gen)
+    results = []
+    t0 = time.time()
+    for c in (cands or candidates(R, dtype)):
+        tan.tune(**c)
+        results.append((time_setting(tan, p, y, reps), c))
+    results.sort(key=lambda r: r[0])
+    best_ms, best = results[0]
+    tan.tune(**best)
+    rec = {"setting": best, "ms": best_ms, "tried": [{"ms": ms, **c} for ms, c in results],
+           "tune_s": time.time() - t0}
+    if cache_path:
+        os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+        cache[key] = rec
+        tmp = cache_path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1)
+        os.replace(tmp, cache_path)
+    return dict(rec, cached=False)

@@ -37,6 +37,7 @@ void eik_opts_default(eik_opts *o)
     o->eik_src_radius = 1.0;
     o->sweep_tol = 1e-12;
     o->sweep_max_cycles = 10000;
+    o->rhs_chunk = 0;
 }
 
 const char *eik_last_error(void) { return eik::last_error(); }
@@ -198,6 +199,19 @@ int tangent_status(eik_tangent *tt, eik_stream stream)
         if (e[0] != 0) { eik::set_error("device fault code %d", e[0]); return EIK_ERR_CUDA; }
         return EIK_OK;
     })
+}
+
+int tangent_tune(eik_tangent *tt, const eik_opts *o)
+{
+    if (!tt || !o) { eik::set_error("bad tangent_tune arguments"); return EIK_ERR_INVALID; }
+    if (o->schedule != EIK_SCHED_PERSISTENT && o->schedule != EIK_SCHED_LEVELS) { eik::set_error("bad schedule"); return EIK_ERR_INVALID; }
+    if (o->rhs_chunk < 0 || o->ctas_per_sm < 0 || !(o->wait_timeout_s > 0)) { eik::set_error("bad tuning values"); return EIK_ERR_INVALID; }
+    Tangent *t = tt->impl;
+    t->opts.schedule = o->schedule;
+    t->opts.ctas_per_sm = o->ctas_per_sm;
+    t->opts.rhs_chunk = o->rhs_chunk;
+    t->opts.wait_timeout_s = o->wait_timeout_s;
+    return EIK_OK;
 }
 
 int tangent_debug_hold(eik_tangent *tt, int source, int step)

@@ -76,7 +76,8 @@ __device__ __forceinline__ unsigned long long global_ns()
 }
 
 struct TravParams {
-    int S, R, n_rec, maxL, nitems;
+    int S, R, n_rec, maxL, nitems;   // R: right-hand sides of this launch (a column chunk)
+    long long ld_in, ld_x, ld_aux;   // row strides (elements) of in, x and aux
     long long N;
     int mode;          // MODE_J or MODE_RAW
     int shared_in;     // forward MODE_J: p is [N][R]
@@ -149,33 +150,33 @@ __device__ __forceinline__ void stage_item(const TravParams &P, Stage<T> &sm, in
     }
 }
 
-// Each group of G lanes owns up to two nodes of the item (slot and slot + nslot); lane l
-// handles right-hand sides l*V .. l*V+V-1, then strides by G*V.  All loads of both
-// nodes (input and up to MAX_ROW upstream values each) are issued before any sum.
+// Each group of G lanes owns up to NPS (1 or 2) nodes of the item (slot, slot + nslot);
+// lane l handles right-hand sides l*V .. l*V+V-1, then strides by G*V.  All loads of
+// the group's nodes (input and up to MAX_ROW upstream values each) are issued before
+// any sum.
 template <typename T, int V, bool TR>
 __device__ __forceinline__ Pack<T, V> node_input(const TravParams &P, int a, int v, int rec, T c, int r)
 {
     const long long N = P.N;
-    const int R = P.R;
     const T *in = reinterpret_cast<const T *>(P.in);
     Pack<T, V> acc;
     if (!TR) {
         if (P.mode == MODE_J) {
-            Pack<T, V> q = load_ro<T, V>(in + ((P.shared_in ? 0 : (long long)a * N) + v) * R + r);
+            Pack<T, V> q = load_ro<T, V>(in + ((P.shared_in ? 0 : (long long)a * N) + v) * P.ld_in + r);
 #pragma unroll
             for (int u = 0; u < V; ++u) acc.v[u] = c * q.v[u];
         } else {
-            acc = load_ro<T, V>(in + ((long long)a * N + v) * R + r);
+            acc = load_ro<T, V>(in + ((long long)a * N + v) * P.ld_in + r);
         }
     } else {
         if (P.mode == MODE_J) {
-            if (rec >= 0) acc = load_ro<T, V>(in + ((long long)a * P.n_rec + rec) * R + r);
+            if (rec >= 0) acc = load_ro<T, V>(in + ((long long)a * P.n_rec + rec) * P.ld_in + r);
             else {
 #pragma unroll
                 for (int u = 0; u < V; ++u) acc.v[u] = T(0);
             }
         } else {
-            acc = load_ro<T, V>(in + ((long long)a * N + v) * R + r);
+            acc = load_ro<T, V>(in + ((long long)a * N + v) * P.ld_in + r);
         }
     }
     return acc;
@@ -186,31 +187,30 @@ __device__ __forceinline__ void node_output(const TravParams &P, int a, int v, i
                                             const Pack<T, V> &acc)
 {
     const long long N = P.N;
-    const int R = P.R;
     T *aux = reinterpret_cast<T *>(P.aux);
-    store<T, V>(x + (long long)v * R + r, acc);
+    store<T, V>(x + (long long)v * P.ld_x + r, acc);
     if (P.mode == MODE_J && aux) {
         if (!TR) {
-            if (rec >= 0) store<T, V>(aux + ((long long)a * P.n_rec + rec) * R + r, acc);
+            if (rec >= 0) store<T, V>(aux + ((long long)a * P.n_rec + rec) * P.ld_aux + r, acc);
         } else if (!P.sum) {
             Pack<T, V> gv;
 #pragma unroll
             for (int u = 0; u < V; ++u) gv.v[u] = c * acc.v[u];
-            store<T, V>(aux + ((long long)a * N + v) * R + r, gv);
+            store<T, V>(aux + ((long long)a * N + v) * P.ld_aux + r, gv);
         }
     }
 }
 
-template <typename T, int V, bool TR>
+template <typename T, int V, bool TR, int NPS>
 __device__ __forceinline__ void run_singletons(const TravParams &P, const Stage<T> &sm, int a, int np, int G)
 {
     const int lane = threadIdx.x % G, slot = threadIdx.x / G, nslot = blockDim.x / G;
     const long long N = P.N;
     const int R = P.R;
-    T *x = reinterpret_cast<T *>(P.x) + a * N * R;
-    for (int k0 = slot; k0 < np; k0 += 2 * nslot) {
+    T *x = reinterpret_cast<T *>(P.x) + a * N * P.ld_x;
+    for (int k0 = slot; k0 < np; k0 += NPS * nslot) {
         const int k1 = k0 + nslot;
-        const bool has1 = k1 < np;
+        const bool has1 = NPS == 2 && k1 < np;
         const int v0 = sm.perm[k0], v1 = has1 ? sm.perm[k1] : -1;
         const bool on0 = v0 >= 0, on1 = v1 >= 0;  // members of nontrivial blocks are skipped
         const int e00 = sm.rp[k0], c0 = on0 ? sm.rp[k0 + 1] - e00 : 0;
@@ -223,8 +223,8 @@ __device__ __forceinline__ void run_singletons(const TravParams &P, const Stage<
             if (on1) a1 = node_input<T, V, TR>(P, a, v1, rec1, cq1, r);
 #pragma unroll
             for (int e = 0; e < MAX_ROW; ++e) {
-                if (e < c0) x0[e] = load_l2<T, V>(x + (long long)sm.en[e00 + e] * R + r);
-                if (e < c1) x1[e] = load_l2<T, V>(x + (long long)sm.en[e01 + e] * R + r);
+                if (e < c0) x0[e] = load_l2<T, V>(x + (long long)sm.en[e00 + e] * P.ld_x + r);
+                if (e < c1) x1[e] = load_l2<T, V>(x + (long long)sm.en[e01 + e] * P.ld_x + r);
             }
 #pragma unroll
             for (int e = 0; e < MAX_ROW; ++e) {
@@ -263,7 +263,7 @@ __device__ void run_block(const TravParams &P, int a, int b)
     const int *en = P.enode + eb;
     const double *ew = P.ew64 + eb;
     const T *in = reinterpret_cast<const T *>(P.in);
-    T *x = reinterpret_cast<T *>(P.x) + a * N * R;
+    T *x = reinterpret_cast<T *>(P.x) + a * N * P.ld_x;
     T *aux = reinterpret_cast<T *>(P.aux);
     double *W = P.ws + wso * R;
     const double *LU = P.lu + luo;
@@ -276,14 +276,14 @@ __device__ void run_block(const TravParams &P, int a, int b)
         const int rec = P.rec_slot[a * N + p];
         if (!TR) {
             if (P.mode == MODE_J)
-                acc = P.cq64[a * N + p] * (double)in[((P.shared_in ? 0 : (long long)a * N) + v) * R + r];
+                acc = P.cq64[a * N + p] * (double)in[((P.shared_in ? 0 : (long long)a * N) + v) * P.ld_in + r];
             else
-                acc = (double)in[((long long)a * N + v) * R + r];
+                acc = (double)in[((long long)a * N + v) * P.ld_in + r];
         } else {
-            if (P.mode == MODE_J) acc = rec >= 0 ? (double)in[((long long)a * P.n_rec + rec) * R + r] : 0.0;
-            else acc = (double)in[((long long)a * N + v) * R + r];
+            if (P.mode == MODE_J) acc = rec >= 0 ? (double)in[((long long)a * P.n_rec + rec) * P.ld_in + r] : 0.0;
+            else acc = (double)in[((long long)a * N + v) * P.ld_in + r];
         }
-        for (int e = rp[p]; e < rp[p + 1]; ++e) acc += ew[e] * (double)__ldcg(x + (long long)en[e] * R + r);
+        for (int e = rp[p]; e < rp[p + 1]; ++e) acc += ew[e] * (double)__ldcg(x + (long long)en[e] * P.ld_x + r);
         W[(long long)m * R + r] = acc;
     }
     __syncthreads();
@@ -327,13 +327,13 @@ __device__ void run_block(const TravParams &P, int a, int b)
         const int p = p0 + m;
         const int v = ~perm[p];
         const double val = W[(long long)m * R + r];
-        x[(long long)v * R + r] = (T)val;
+        x[(long long)v * P.ld_x + r] = (T)val;
         if (P.mode == MODE_J && aux) {
             const int rec = P.rec_slot[a * N + p];
             if (!TR) {
-                if (rec >= 0) aux[((long long)a * P.n_rec + rec) * R + r] = (T)val;
+                if (rec >= 0) aux[((long long)a * P.n_rec + rec) * P.ld_aux + r] = (T)val;
             } else if (!P.sum) {
-                aux[((long long)a * N + v) * R + r] = (T)(P.cq64[a * N + p] * val);
+                aux[((long long)a * N + v) * P.ld_aux + r] = (T)(P.cq64[a * N + p] * val);
             }
         }
     }
@@ -345,11 +345,14 @@ __device__ __forceinline__ void run_item(const TravParams &P, Stage<T> &sm, int4
     if (it.z >= 0) {
         stage_item<T>(P, sm, it.x, it.z, it.w, eb);
         __syncthreads();
-        run_singletons<T, V, TR>(P, sm, it.x, it.w - it.z, G);
+        run_singletons<T, V, TR, 2>(P, sm, it.x, it.w - it.z, G);
     } else {
         run_block<T, TR>(P, it.x, ~it.z);
     }
 }
+
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // ---------------------------------------------------------------- persistent schedule
 template <typename T, int V, bool TR>
@@ -396,12 +399,32 @@ __global__ void __launch_bounds__(256) k_traverse_persistent(TravParams P, int G
 }
 
 // ---------------------------------------------------------------- per-level schedule
-template <typename T, int V, bool TR>
-__global__ void __launch_bounds__(256) k_traverse_step(TravParams P, int G, int first)
+// One launch per step: every CTA runs one item, with no ticket, wait or counter.  The
+// launches are chained with programmatic dependent launch: a CTA stages its item's
+// structure (never written by the traversal) before griddepcontrol.wait, so staging
+// overlaps the tail of the previous level; after the wait every value of earlier levels
+// is complete and visible.  Parameters are read from device memory, so a captured
+// sequence of these launches does not depend on the caller's buffers.
+template <typename T, int V, bool TR, int NPS>
+__global__ void __launch_bounds__(512) k_traverse_level(const TravParams *__restrict__ Pd, int G, int first)
 {
     __shared__ Stage<T> sm;
-    run_item<T, V, TR>(P, sm, P.items[first + blockIdx.x], P.ebeg[first + blockIdx.x], G);
+    const TravParams &P = *Pd;
+    const int i = first + blockIdx.x;
+    const int4 it = P.items[i];
+    grid_dependents_launch();
+    if (it.z >= 0) {
+        stage_item<T>(P, sm, it.x, it.z, it.w, P.ebeg[i]);
+        grid_dependency_wait();
+        __syncthreads();
+        run_singletons<T, V, TR, NPS>(P, sm, it.x, it.w - it.z, G);
+    } else {
+        grid_dependency_wait();
+        run_block<T, TR>(P, it.x, ~it.z);
+    }
 }
+
+__global__ void k_set_params(TravParams *Pd, TravParams P) { *Pd = P; }
 
 // g[j][r] = sum_a cq_a[j] lam_a[j][r] in source order.  FP64 path: FP64 products and
 // sum.  FP32 path: FP32 products with a compensated (Kahan) FP32 sum, so the rounding
@@ -411,17 +434,19 @@ constexpr int SUMB = 8;
 
 template <typename T>
 __global__ void k_source_sum(long long N, int S, int R, const T *__restrict__ cqn, const T *__restrict__ lam,
-                             T *__restrict__ g)
+                             long long ld_lam, T *__restrict__ g, long long ld_g)
 {
-    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= N * R) return;
-    long long j = idx / R;
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= N * R) return;
+    long long j = t / R;
+    int r = (int)(t - j * R);
+    long long idx = j * ld_lam + r;
     T acc = 0, comp = 0;
     for (int a0 = 0; a0 < S; a0 += SUMB) {
         T vals[SUMB];
 #pragma unroll
         for (int b = 0; b < SUMB; ++b)
-            vals[b] = a0 + b < S ? __ldg(cqn + (long long)(a0 + b) * N + j) * __ldcs(lam + (long long)(a0 + b) * N * R + idx) : T(0);
+            vals[b] = a0 + b < S ? __ldg(cqn + (long long)(a0 + b) * N + j) * __ldcs(lam + (long long)(a0 + b) * N * ld_lam + idx) : T(0);
 #pragma unroll
         for (int b = 0; b < SUMB; ++b) {
             if (sizeof(T) == 8) {
@@ -434,7 +459,7 @@ __global__ void k_source_sum(long long N, int S, int R, const T *__restrict__ cq
             }
         }
     }
-    g[idx] = acc;
+    g[j * ld_g + r] = acc;
 }
 
 // receiver sampling P: out[a][k] = field[a][rec[a][k]]
@@ -473,20 +498,66 @@ int ensure_workspace(Tangent *t, size_t vec_bytes, size_t blk_elems)
     return EIK_OK;
 }
 
+template <typename T, int V, bool TR, int NPS>
+static int launch_levels(Tangent *t, int G, int threads, int first_step, TravParams *Pd, cudaStream_t st)
+{
+    const std::vector<int> &sp = TR ? t->step_ptr_bwd : t->step_ptr_fwd;
+    for (int s = first_step; s < t->maxL; ++s) {
+        int n = sp[s + 1] - sp[s];
+        if (n <= 0) continue;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)n);
+        cfg.blockDim = dim3((unsigned)threads);
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        // the first level follows the parameter upload: launch it fully ordered
+        cfg.attrs = attr;
+        cfg.numAttrs = s == first_step ? 0 : 1;
+        EIK_CHECK(cudaLaunchKernelEx(&cfg, k_traverse_level<T, V, TR, NPS>, (const TravParams *)Pd, G, sp[s]));
+    }
+    return EIK_OK;
+}
+
 template <typename T, int V, bool TR>
 static int launch_traverse(Tangent *t, TravParams &P, int G, cudaStream_t st)
 {
-    // a CTA holds ITEM_MAX / 2 node slots of G lanes (two nodes per slot), at most 256 threads
-    const int threads = std::min(256, std::max(32, ITEM_MAX * G / 2));
     if (t->opts.schedule == EIK_SCHED_LEVELS) {
-        const std::vector<int> &sp = TR ? t->step_ptr_bwd : t->step_ptr_fwd;
-        for (int s = 0; s < t->maxL; ++s) {
-            int n = sp[s + 1] - sp[s];
-            if (n > 0) k_traverse_step<T, V, TR><<<n, threads, 0, st>>>(P, G, sp[s]);
-        }
+        // one item per CTA, one node per slot (two when a CTA would exceed 512 threads)
+        const bool two = ITEM_MAX * G > 512;
+        const int threads = std::max(32, two ? ITEM_MAX * G / 2 : ITEM_MAX * G);
+        if (!t->params_d) EIK_CHECK(cudaMalloc(&t->params_d, 2 * sizeof(TravParams)));
+        TravParams *Pd = t->params_d + (TR ? 1 : 0);
+        k_set_params<<<1, 1, 0, st>>>(Pd, P);
         EIK_CHECK_LAUNCH();
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        EIK_CHECK(cudaStreamIsCapturing(st, &cs));
+        if (cs != cudaStreamCaptureStatusNone || !t->opts_graph) {
+            // the caller is capturing (or graphs are off): launch directly into its stream
+            return two ? launch_levels<T, V, TR, 2>(t, G, threads, 0, Pd, st)
+                       : launch_levels<T, V, TR, 1>(t, G, threads, 0, Pd, st);
+        }
+        const long long key = ((long long)TR << 40) | ((long long)sizeof(T) << 32) | ((long long)V << 16) | G;
+        cudaGraphExec_t &exec = t->level_graphs[key];
+        if (!exec) {
+            if (!t->cap_stream) EIK_CHECK(cudaStreamCreateWithFlags(&t->cap_stream, cudaStreamNonBlocking));
+            EIK_CHECK(cudaStreamBeginCapture(t->cap_stream, cudaStreamCaptureModeThreadLocal));
+            int rc = two ? launch_levels<T, V, TR, 2>(t, G, threads, 0, Pd, t->cap_stream)
+                         : launch_levels<T, V, TR, 1>(t, G, threads, 0, Pd, t->cap_stream);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(t->cap_stream, &g);
+            if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+            e = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) { exec = nullptr; return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__); }
+        }
+        EIK_CHECK(cudaGraphLaunch(exec, st));
         return EIK_OK;
     }
+    // persistent: a CTA holds ITEM_MAX / 2 node slots of G lanes (two nodes per slot)
+    const int threads = std::min(256, std::max(32, ITEM_MAX * G / 2));
     int per_sm = t->opts.ctas_per_sm;
     if (per_sm <= 0) {
         EIK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_persistent<T, V, TR>, threads, 0));
@@ -506,9 +577,10 @@ static int dispatch_v(Tangent *t, TravParams &P, cudaStream_t st)
 {
     // widest vector that divides R and keeps every row 16-byte aligned when possible
     const int R = P.R;
+    auto fits = [&](int v) { return R % v == 0 && P.ld_in % v == 0 && P.ld_x % v == 0 && P.ld_aux % v == 0; };
     int V = 1;
-    if (sizeof(T) == 4 && R % 4 == 0) V = 4;
-    else if (R % 2 == 0) V = 2;
+    if (sizeof(T) == 4 && fits(4)) V = 4;
+    else if (fits(2)) V = 2;
     int lanes = (R + V - 1) / V;
     int G = 1;
     while (G < lanes && G < 32) G <<= 1;
@@ -533,45 +605,56 @@ int traverse(Tangent *t, bool TR, int mode, const void *in, int shared_in, int R
     const void *ptrs[3] = {in, out_full, out_aux};
     for (const void *p : ptrs)
         if (p && !aligned16(p)) { set_error("device buffers must be 16-byte aligned"); return EIK_ERR_INVALID; }
-    const size_t vec_bytes = (size_t)t->S * t->N * R * esz;
-    void *x = out_full;
-    size_t need_vec = x ? 0 : vec_bytes;
-    int rc = ensure_workspace(t, need_vec, (size_t)t->ws_rows * R);
+    // right-hand sides are processed in column chunks of Rc (all of R by default); a chunk
+    // is a column slice of the caller's [.][R] buffers, so only the workspace shrinks
+    int Rc = R;
+    if (t->opts.rhs_chunk > 0 && t->opts.rhs_chunk < R) {
+        Rc = t->opts.rhs_chunk;
+        const int unit = dtype == EIK_F32 ? 4 : 2;
+        if (R % unit == 0) Rc = std::max(unit, Rc / unit * unit);
+    }
+    size_t need_vec = out_full ? 0 : (size_t)t->S * t->N * Rc * esz;
+    int rc = ensure_workspace(t, need_vec, (size_t)t->ws_rows * Rc);
     if (rc) return rc;
-    if (!x) x = t->ws_vec;
-    TravParams P{};
-    P.S = t->S; P.R = R; P.n_rec = t->n_rec; P.maxL = t->maxL; P.nitems = t->nitems; P.N = t->N;
-    P.mode = mode; P.shared_in = shared_in; P.sum = sum_sources;
-    P.perm = t->perm;
-    P.rowptr = TR ? t->cptr : t->rowptr;
-    P.enode = TR ? t->dn_node : t->up_node;
-    P.ew = dtype == EIK_F32 ? (const void *)(TR ? t->dn_w32 : t->up_w32) : (const void *)(TR ? t->dn_w64 : t->up_w64);
-    P.ew64 = TR ? t->dn_w64 : t->up_w64;
-    P.ebase = nullptr;
-    P.cq = dtype == EIK_F32 ? (const void *)t->cq32 : (const void *)t->cq64;
-    P.cq64 = t->cq64;
-    P.rec_slot = t->rec_slot;
-    P.in = in; P.x = x; P.aux = out_aux;
-    P.items = TR ? t->items_bwd : t->items_fwd;
-    P.ebeg = TR ? t->ebeg_bwd : t->ebeg_fwd;
-    P.item_cnt = t->item_cnt + (TR ? (size_t)t->S * t->maxL : 0);
-    P.done = t->done; P.ticket = t->ticket; P.err = t->err;
-    P.blk_desc = t->blk_desc; P.blk_off = t->blk_off; P.lu = t->lu; P.piv = t->piv; P.ws = t->ws_blk;
-    P.timeout_ns = (unsigned long long)(t->opts.wait_timeout_s * 1e9);
-    // per-source edge bases live on the device next to the items
-    static_assert(sizeof(long long) == 8, "");
-    P.ebase = TR ? reinterpret_cast<const long long *>(t->tbase_d) : reinterpret_cast<const long long *>(t->ebase_d);
-    if (dtype == EIK_F32) rc = TR ? dispatch_v<float, true>(t, P, st) : dispatch_v<float, false>(t, P, st);
-    else rc = TR ? dispatch_v<double, true>(t, P, st) : dispatch_v<double, false>(t, P, st);
-    if (rc) return rc;
-    if (TR && mode == MODE_J && sum_sources && out_aux) {
-        long long n = t->N * R;
-        unsigned blocks = (unsigned)((n + 255) / 256);
-        if (dtype == EIK_F32)
-            k_source_sum<float><<<blocks, 256, 0, st>>>(t->N, t->S, R, t->cqn32, (const float *)x, (float *)out_aux);
-        else
-            k_source_sum<double><<<blocks, 256, 0, st>>>(t->N, t->S, R, t->cqn64, (const double *)x, (double *)out_aux);
-        EIK_CHECK_LAUNCH();
+    for (int r0 = 0; r0 < R; r0 += Rc) {
+        const int w = std::min(Rc, R - r0);
+        const char *inp = static_cast<const char *>(in) + r0 * esz;
+        char *xp = out_full ? static_cast<char *>(out_full) + r0 * esz : static_cast<char *>(t->ws_vec);
+        char *auxp = out_aux ? static_cast<char *>(out_aux) + r0 * esz : nullptr;
+        TravParams P{};
+        P.S = t->S; P.R = w; P.n_rec = t->n_rec; P.maxL = t->maxL; P.nitems = t->nitems; P.N = t->N;
+        P.ld_in = R; P.ld_x = out_full ? R : w; P.ld_aux = R;
+        P.mode = mode; P.shared_in = shared_in; P.sum = sum_sources;
+        P.perm = t->perm;
+        P.rowptr = TR ? t->cptr : t->rowptr;
+        P.enode = TR ? t->dn_node : t->up_node;
+        P.ew = dtype == EIK_F32 ? (const void *)(TR ? t->dn_w32 : t->up_w32) : (const void *)(TR ? t->dn_w64 : t->up_w64);
+        P.ew64 = TR ? t->dn_w64 : t->up_w64;
+        P.ebase = TR ? t->tbase_d : t->ebase_d;
+        P.cq = dtype == EIK_F32 ? (const void *)t->cq32 : (const void *)t->cq64;
+        P.cq64 = t->cq64;
+        P.rec_slot = t->rec_slot;
+        P.in = inp; P.x = xp; P.aux = auxp;
+        P.items = TR ? t->items_bwd : t->items_fwd;
+        P.ebeg = TR ? t->ebeg_bwd : t->ebeg_fwd;
+        P.item_cnt = t->item_cnt + (TR ? (size_t)t->S * t->maxL : 0);
+        P.done = t->done; P.ticket = t->ticket; P.err = t->err;
+        P.blk_desc = t->blk_desc; P.blk_off = t->blk_off; P.lu = t->lu; P.piv = t->piv; P.ws = t->ws_blk;
+        P.timeout_ns = (unsigned long long)(t->opts.wait_timeout_s * 1e9);
+        if (dtype == EIK_F32) rc = TR ? dispatch_v<float, true>(t, P, st) : dispatch_v<float, false>(t, P, st);
+        else rc = TR ? dispatch_v<double, true>(t, P, st) : dispatch_v<double, false>(t, P, st);
+        if (rc) return rc;
+        if (TR && mode == MODE_J && sum_sources && out_aux) {
+            long long n = t->N * w;
+            unsigned blocks = (unsigned)((n + 255) / 256);
+            if (dtype == EIK_F32)
+                k_source_sum<float><<<blocks, 256, 0, st>>>(t->N, t->S, w, t->cqn32, (const float *)xp, P.ld_x,
+                                                            (float *)auxp, (long long)R);
+            else
+                k_source_sum<double><<<blocks, 256, 0, st>>>(t->N, t->S, w, t->cqn64, (const double *)xp, P.ld_x,
+                                                             (double *)auxp, (long long)R);
+            EIK_CHECK_LAUNCH();
+        }
     }
     return EIK_OK;
 }

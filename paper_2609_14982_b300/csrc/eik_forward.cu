@@ -12,8 +12,8 @@
 // After every ordering each boundary node takes the value of its nearest interior node
 // along the inward diagonal (one step inward along every boundary axis), which keeps
 // the iteration monotone.  Nodes within eik_src_radius * max(h) of the source keep
-// tau = 1.  Start: tau = 1.  Stop: the largest |change| over one full cycle is below
-// eik_tol.
+// tau = 1.  Start: tau = 1.  Stop, per source: the first cycle whose largest |change|
+// for that source is below eik_tol (that source then stops iterating).
 // Compiled with -fmad=false so that every step is a separately rounded IEEE operation.
 #include <cuda_runtime.h>
 
@@ -60,8 +60,9 @@ struct LFParams {
     int S, order, h, lo0, hi0;
     const double *G, *s, *T0, *g0, *alpha;
     const unsigned char *fixed;
+    const unsigned char *active;   // [S] sources still iterating
     double *tau;
-    unsigned long long *dmax;   // bit pattern of max |d tau| (non-negative double)
+    unsigned long long *dmax;   // [S] bit pattern of max |d tau| per source (non-negative double)
 };
 
 __device__ __forceinline__ double lf_update(const LFParams &P, long long a, long long i, const int *c)
@@ -102,6 +103,7 @@ __global__ void k_lf_plane(LFParams P)
     const long long span = (long long)(P.hi0 - P.lo0 + 1) * (nd == 3 ? m1 : 1);
     if (tid >= span * P.S) return;
     long long a = tid / span, cell = tid - a * span;
+    if (!P.active[a]) return;
     int c0, c1, c2;
     if (nd == 3) {
         c0 = P.lo0 + (int)(cell / m1);
@@ -125,16 +127,17 @@ __global__ void k_lf_plane(LFParams P)
     double old = P.tau[v];
     P.tau[v] = nv;
     double dd = fabs(nv - old);
-    atomicMax(P.dmax, (unsigned long long)__double_as_longlong(dd));
+    atomicMax(P.dmax + a, (unsigned long long)__double_as_longlong(dd));
 }
 
 // boundary nodes take the value of the nearest interior node along the inward diagonal
-__global__ void k_lf_boundary(GridDesc g, int S, const unsigned char *__restrict__ fixed, double *tau,
-                              unsigned long long *dmax)
+__global__ void k_lf_boundary(GridDesc g, int S, const unsigned char *__restrict__ fixed,
+                              const unsigned char *__restrict__ active, double *tau, unsigned long long *dmax)
 {
     long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (v >= g.N * S || fixed[v]) return;
     long long a = v / g.N, i = v - a * g.N;
+    if (!active[a]) return;
     int c[3];
     if (g.ndim == 3) { c[2] = (int)(i % g.n[2]); c[1] = (int)((i / g.n[2]) % g.n[1]); c[0] = (int)(i / g.st[0]); }
     else { c[1] = (int)(i % g.n[1]); c[0] = (int)(i / g.n[1]); c[2] = 0; }
@@ -148,7 +151,7 @@ __global__ void k_lf_boundary(GridDesc g, int S, const unsigned char *__restrict
     double nv = ta[i + step];
     double dd = fabs(nv - ta[i]);
     ta[i] = nv;
-    atomicMax(dmax, (unsigned long long)__double_as_longlong(dd));
+    atomicMax(dmax + a, (unsigned long long)__double_as_longlong(dd));
 }
 
 __global__ void k_eik_out(long long SN, const double *T0, const double *tau, double *T)
@@ -181,12 +184,12 @@ extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const in
         const int nd = g.ndim;
         const long long N = g.N, SN = N * S;
         double *G = nullptr, *Jm = nullptr, *T0 = nullptr, *g0 = nullptr, *alpha = nullptr, *tau = nullptr;
-        unsigned char *fixed = nullptr;
+        unsigned char *fixed = nullptr, *active = nullptr;
         int *src_d = nullptr;
         unsigned long long *dmax = nullptr;
         auto release = [&]() {
             cudaFree(G); cudaFree(Jm); cudaFree(T0); cudaFree(g0); cudaFree(alpha); cudaFree(tau);
-            cudaFree(fixed); cudaFree(src_d); cudaFree(dmax);
+            cudaFree(fixed); cudaFree(active); cudaFree(src_d); cudaFree(dmax);
         };
 #define TRY(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { int rc_ = cuda_fail(e_, #call, __FILE__, __LINE__); release(); return rc_; } } while (0)
         TRY(cudaMalloc(&G, N * nd * nd * sizeof(double)));
@@ -197,7 +200,8 @@ extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const in
         TRY(cudaMalloc(&tau, SN * sizeof(double)));
         TRY(cudaMalloc(&fixed, SN));
         TRY(cudaMalloc(&src_d, S * sizeof(int)));
-        TRY(cudaMalloc(&dmax, sizeof(unsigned long long)));
+        TRY(cudaMalloc(&dmax, S * sizeof(unsigned long long)));
+        TRY(cudaMalloc(&active, S));
         TRY(cudaMemcpyAsync(src_d, src_node, S * sizeof(int), cudaMemcpyHostToDevice, st));
         double hmax = 0.0;
         for (int d = 0; d < nd; ++d) hmax = std::max(hmax, g.dxi[d]);
@@ -207,13 +211,17 @@ extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const in
         TRY(cudaGetLastError());
         LFParams P{};
         P.g = g; P.S = S; P.G = G; P.s = s; P.T0 = T0; P.g0 = g0; P.alpha = alpha; P.fixed = fixed; P.tau = tau;
-        P.dmax = dmax;
+        P.dmax = dmax; P.active = active;
         const int m0 = g.n[0] - 2, m1 = g.n[1] - 2, m2 = nd == 3 ? g.n[2] - 2 : 1;
         const int hmax_i = (m0 - 1) + (m1 - 1) + (nd == 3 ? m2 - 1 : 0);
         const int nord = 1 << nd;
-        int used = -1;
+        // each source stops at the first cycle whose largest change is below eik_tol
+        std::vector<unsigned char> h_active(S, 1);
+        std::vector<unsigned long long> h_dmax(S);
+        TRY(cudaMemcpyAsync(active, h_active.data(), S, cudaMemcpyHostToDevice, st));
+        int used = -1, left = S;
         for (int cyc = 1; cyc <= opts->eik_max_cycles; ++cyc) {
-            TRY(cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), st));
+            TRY(cudaMemsetAsync(dmax, 0, S * sizeof(unsigned long long), st));
             for (int o = 0; o < nord; ++o) {
                 P.order = o;
                 for (int h = 0; h <= hmax_i; ++h) {
@@ -224,15 +232,20 @@ extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const in
                     long long span = (long long)(P.hi0 - P.lo0 + 1) * (nd == 3 ? m1 : 1) * S;
                     k_lf_plane<<<(unsigned)((span + 255) / 256), 256, 0, st>>>(P);
                 }
-                k_lf_boundary<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(g, S, fixed, tau, dmax);
+                k_lf_boundary<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(g, S, fixed, active, tau, dmax);
             }
             TRY(cudaGetLastError());
-            unsigned long long hb = 0;
-            TRY(cudaMemcpyAsync(&hb, dmax, sizeof hb, cudaMemcpyDeviceToHost, st));
+            TRY(cudaMemcpyAsync(h_dmax.data(), dmax, S * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
             TRY(cudaStreamSynchronize(st));
-            double dm;
-            std::memcpy(&dm, &hb, sizeof dm);
-            if (dm < opts->eik_tol) { used = cyc; break; }
+            bool changed = false;
+            for (int a = 0; a < S; ++a) {
+                if (!h_active[a]) continue;
+                double dm;
+                std::memcpy(&dm, &h_dmax[a], sizeof dm);
+                if (dm < opts->eik_tol) { h_active[a] = 0; --left; changed = true; }
+            }
+            if (left == 0) { used = cyc; break; }
+            if (changed) TRY(cudaMemcpyAsync(active, h_active.data(), S, cudaMemcpyHostToDevice, st));
         }
         k_eik_out<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(SN, T0, tau, T);
         TRY(cudaGetLastError());

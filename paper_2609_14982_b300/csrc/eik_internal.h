@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -11,6 +12,7 @@
 
 namespace eik {
 
+struct TravParams;
 void set_error(const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
 
@@ -118,6 +120,12 @@ struct Tangent {
     size_t ws_blk_elems = 0;
     int host_err = 0;
     std::vector<long long> holds;   // item_cnt entries raised by tangent_debug_hold
+    // per-level schedule: device-resident launch parameters (forward, transpose) and the
+    // captured level sequences, keyed by (direction, element size, vector width, lanes)
+    struct TravParams *params_d = nullptr;
+    std::map<long long, cudaGraphExec_t> level_graphs;
+    cudaStream_t cap_stream = nullptr;
+    bool opts_graph = true;
 };
 
 int build_tangent(const eik_grid *g, const double *T, const double *s, int S, const int *src_node,

@@ -26,10 +26,12 @@ __global__ void k_l_axpby_sq(long long n, const T *__restrict__ a, T *__restrict
 {
     // u = a - sign * sc[coef] * u ;  partial[block] = sum u^2 over the block's stride
     __shared__ double red[LB];
-    double coef = coef_slot >= 0 ? sign * sc[coef_slot] : 0.0;
+    // coef_slot < 0: u = a (u is not read, so it may hold anything, e.g. fresh memory)
+    const bool axpby = coef_slot >= 0;
+    double coef = axpby ? sign * sc[coef_slot] : 0.0;
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)LB + threadIdx.x; i < n; i += (long long)gridDim.x * LB) {
-        double v = (double)a[i] - coef * (double)u[i];
+        double v = axpby ? (double)a[i] - coef * (double)u[i] : (double)a[i];
         T tv = (T)v;
         u[i] = tv;
         acc += (double)tv * (double)tv;

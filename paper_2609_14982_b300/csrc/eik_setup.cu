@@ -732,6 +732,9 @@ void free_tangent(Tangent *t)
                     t->piv, t->items_fwd, t->items_bwd, t->ebeg_fwd, t->ebeg_bwd, t->item_cnt, t->done, t->ticket, t->err, t->ws_vec,
                     t->ws_blk, t->ebase_d, t->tbase_d};
     for (void *p : ptrs) if (p) cudaFree(p);
+    if (t->params_d) cudaFree((void *)t->params_d);
+    for (auto &kv : t->level_graphs) if (kv.second) cudaGraphExecDestroy(kv.second);
+    if (t->cap_stream) cudaStreamDestroy(t->cap_stream);
     delete t;
 }
 

@@ -23,7 +23,7 @@ STATUS = {0: "OK", -1: "INVALID", -2: "OOM", -3: "SINGULAR_BLOCK", -4: "NOT_CONV
 
 EXPORTED = ["eik_opts_default", "eik_last_error", "eik_version", "eik_forward", "tangent_build", "tangent_apply",
             "tangent_apply_T", "tangent_solve", "tangent_solve_T", "tangent_sample", "tangent_stats", "tangent_dims",
-            "tangent_export", "tangent_status", "tangent_free", "sweep_apply", "tangent_debug_hold",
+            "tangent_export", "tangent_status", "tangent_free", "sweep_apply", "tangent_debug_hold", "tangent_tune",
             "lsqr_create", "lsqr_start", "lsqr_iterate", "lsqr_solution", "lsqr_free"]
 
 
@@ -41,7 +41,7 @@ class Opts(C.Structure):
     _fields_ = [("model", C.c_int), ("lu_pivot_tol", C.c_double), ("schedule", C.c_int), ("threads", C.c_int),
                 ("chunk", C.c_int), ("ctas_per_sm", C.c_int), ("wait_timeout_s", C.c_double),
                 ("eik_tol", C.c_double), ("eik_max_cycles", C.c_int), ("eik_src_radius", C.c_double),
-                ("sweep_tol", C.c_double), ("sweep_max_cycles", C.c_int)]
+                ("sweep_tol", C.c_double), ("sweep_max_cycles", C.c_int), ("rhs_chunk", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -80,6 +80,7 @@ def lib():
         L.tangent_free.argtypes = [P]
         L.tangent_free.restype = None
         L.tangent_debug_hold.argtypes = [P, I, I]
+        L.tangent_tune.argtypes = [P, C.POINTER(Opts)]
         L.lsqr_create.argtypes = [P, I, C.POINTER(P)]
         L.lsqr_start.argtypes = [P, P, P]
         L.lsqr_iterate.argtypes = [P, I, I, P]
@@ -238,6 +239,14 @@ class Tangent:
         _check(lib().sweep_apply(self.h, int(transpose), _dev(b, name="b"), b.shape[-1], _dev(out, b.dtype, "x"),
                                  _dt(b.dtype), C.byref(opts) if opts else None, C.byref(cyc), _stream()))
         return out, cyc.value
+
+    def tune(self, **kw):
+        """Change run-time options (schedule, ctas_per_sm, rhs_chunk, wait_timeout_s)."""
+        for k, v in kw.items():
+            if k not in ("schedule", "ctas_per_sm", "rhs_chunk", "wait_timeout_s"):
+                raise KeyError(k)
+            setattr(self.opts, k, v)
+        _check(lib().tangent_tune(self.h, C.byref(self.opts)))
 
     def debug_hold(self, source: int, step: int):
         """Test hook: make the persistent traversal's wait before (source, step) run out."""
