@@ -126,6 +126,30 @@ const char *eik_version(void);
 int eik_forward(const eik_grid *g, const double *s, int S, const int *src_node,
                 double *T, const eik_opts *opts, int *cycles, eik_stream stream);
 
+/*
+ * eik_forward_noalloc -- the paper has no counterpart to this call; it exists for
+ * callers that cannot allocate device memory, for example code running inside a
+ * framework whose caching allocator owns all device memory, or inside a region
+ * where cudaMalloc and cudaFree are not allowed (they synchronize the device).
+ * It computes exactly what eik_forward computes, with the same arguments, but calls no
+ * allocator: its scratch is one file-scope device array of
+ * eik_forward_noalloc_capacity() bytes (64 MiB), held by every GPU that loads the
+ * library until the process exits.
+ *   Limit: the call needs 2 N ndim^2 + S N (2 + 2 ndim) doubles + S N bytes (+ small
+ *   alignment); larger requests return EIK_ERR_INVALID with the sizes in the message
+ *   (about 320k 3-D nodes for one source).
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call before any
+ *   stream capture.
+ *   Sharing: every call, on any stream, uses the same array and overwrites it; calls
+ *   that overlap on the GPU race with each other.  Issue them one after the other.
+ */
+int eik_forward_noalloc(const eik_grid *g, const double *s, int S, const int *src_node,
+                        double *T, const eik_opts *opts, int *cycles, eik_stream stream);
+
+/* Bytes of the fixed scratch array behind eik_forward_noalloc. */
+size_t eik_forward_noalloc_capacity(void);
+
 typedef struct eik_tangent eik_tangent;
 
 /*

@@ -260,3 +260,162 @@ extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const in
         return EIK_ERR_INVALID;
     }
 }
+
+// ---------------------------------------------------------------------------------
+// eik_forward_noalloc: the same state solve for callers that must not allocate device
+// memory.  Its scratch lives in one file-scope device array of fixed size instead of
+// cudaMalloc'd buffers.  Host code may not pass the array's name to a kernel (on the
+// host it is only a stand-in symbol); the device address is looked up once per device
+// with cudaGetSymbolAddress, with that device current, on the first call there.
+// ---------------------------------------------------------------------------------
+#include <mutex>
+
+#define EIK_NOALLOC_SCRATCH_BYTES (64ull << 20)
+
+static __device__ __align__(256) unsigned char g_eik_noalloc_scratch[EIK_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_addr[kMaxDevices] = {nullptr};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// bytes of scratch one call needs (same buffers eik_forward allocates)
+size_t noalloc_bytes(int nd, long long N, int S)
+{
+    const long long SN = N * S;
+    size_t b = 0;
+    b += align256((size_t)N * nd * nd * sizeof(double));     // G
+    b += align256((size_t)N * nd * nd * sizeof(double));     // J
+    b += align256((size_t)SN * sizeof(double));              // T0
+    b += align256((size_t)SN * nd * sizeof(double));         // g0
+    b += align256((size_t)SN * nd * sizeof(double));         // alpha
+    b += align256((size_t)SN * sizeof(double));              // tau
+    b += align256((size_t)SN);                               // fixed flags
+    b += align256((size_t)S * sizeof(int));                  // source nodes
+    b += align256((size_t)S * sizeof(unsigned long long));   // max change per source
+    b += align256((size_t)S);                                // active flags
+    return b;
+}
+
+int scratch_for_current_device(unsigned char **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice", __FILE__, __LINE__);
+    if (dev < 0 || dev >= kMaxDevices) { set_error("device index %d not supported", dev); return EIK_ERR_INVALID; }
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_eik_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress", __FILE__, __LINE__);
+        g_scratch_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_scratch_addr[dev]);
+    return EIK_OK;
+}
+}  // namespace
+
+extern "C" size_t eik_forward_noalloc_capacity(void) { return (size_t)EIK_NOALLOC_SCRATCH_BYTES; }
+
+extern "C" int eik_forward_noalloc(const eik_grid *gin, const double *s, int S, const int *src_node, double *T,
+                                   const eik_opts *opts_in, int *cycles, eik_stream stream)
+{
+    try {
+        if (!gin || (gin->ndim != 2 && gin->ndim != 3) || !gin->xyz || !s || !T || !src_node || S <= 0) {
+            set_error("bad eik_forward_noalloc arguments");
+            return EIK_ERR_INVALID;
+        }
+        eik_opts def;
+        eik_opts_default(&def);
+        const eik_opts *opts = opts_in ? opts_in : &def;
+        GridDesc g = make_grid_desc(gin);
+        for (int d = 0; d < g.ndim; ++d)
+            if (g.n[d] < 3) { set_error("grid needs >= 3 nodes per axis"); return EIK_ERR_INVALID; }
+        for (int a = 0; a < S; ++a)
+            if (src_node[a] < 0 || src_node[a] >= g.N) { set_error("source node out of range"); return EIK_ERR_INVALID; }
+        const int nd = g.ndim;
+        const long long N = g.N, SN = N * S;
+        const size_t need = noalloc_bytes(nd, N, S);
+        if (need > EIK_NOALLOC_SCRATCH_BYTES) {
+            set_error("eik_forward_noalloc needs %zu bytes of scratch for %d sources x %lld nodes; its fixed "
+                      "scratch holds %zu bytes (use eik_forward)", need, S, N, (size_t)EIK_NOALLOC_SCRATCH_BYTES);
+            return EIK_ERR_INVALID;
+        }
+        unsigned char *base = nullptr;
+        int rc = scratch_for_current_device(&base);
+        if (rc) return rc;
+        size_t off = 0;
+        auto carve = [&](size_t bytes) { unsigned char *p = base + off; off += align256(bytes); return p; };
+        double *G = (double *)carve((size_t)N * nd * nd * sizeof(double));
+        double *Jm = (double *)carve((size_t)N * nd * nd * sizeof(double));
+        double *T0 = (double *)carve((size_t)SN * sizeof(double));
+        double *g0 = (double *)carve((size_t)SN * nd * sizeof(double));
+        double *alpha = (double *)carve((size_t)SN * nd * sizeof(double));
+        double *tau = (double *)carve((size_t)SN * sizeof(double));
+        unsigned char *fixed = carve((size_t)SN);
+        int *src_d = (int *)carve((size_t)S * sizeof(int));
+        unsigned long long *dmax = (unsigned long long *)carve((size_t)S * sizeof(unsigned long long));
+        unsigned char *active = carve((size_t)S);
+        cudaStream_t st = (cudaStream_t)stream;
+#define TRY(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return cuda_fail(e_, #call, __FILE__, __LINE__); } while (0)
+        TRY(cudaMemcpyAsync(src_d, src_node, S * sizeof(int), cudaMemcpyHostToDevice, st));
+        double hmax = 0.0;
+        for (int d = 0; d < nd; ++d) hmax = std::max(hmax, g.dxi[d]);
+        // every buffer is fully rewritten below (tau by the prep kernel, dmax per cycle),
+        // so contents left by an earlier call do not matter
+        k_metric<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(g, gin->xyz, G, Jm);
+        k_eik_prep<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(g, S, gin->xyz, Jm, G, s, src_d,
+                                                                  opts->eik_src_radius * hmax, T0, g0, alpha, fixed, tau);
+        TRY(cudaGetLastError());
+        LFParams P{};
+        P.g = g; P.S = S; P.G = G; P.s = s; P.T0 = T0; P.g0 = g0; P.alpha = alpha; P.fixed = fixed; P.tau = tau;
+        P.dmax = dmax; P.active = active;
+        const int m0 = g.n[0] - 2, m1 = g.n[1] - 2, m2 = nd == 3 ? g.n[2] - 2 : 1;
+        const int hmax_i = (m0 - 1) + (m1 - 1) + (nd == 3 ? m2 - 1 : 0);
+        const int nord = 1 << nd;
+        // each source stops at the first cycle whose largest change is below eik_tol
+        std::vector<unsigned char> h_active(S, 1);
+        std::vector<unsigned long long> h_dmax(S);
+        TRY(cudaMemcpyAsync(active, h_active.data(), S, cudaMemcpyHostToDevice, st));
+        int used = -1, left = S;
+        for (int cyc = 1; cyc <= opts->eik_max_cycles; ++cyc) {
+            TRY(cudaMemsetAsync(dmax, 0, S * sizeof(unsigned long long), st));
+            for (int o = 0; o < nord; ++o) {
+                P.order = o;
+                for (int h = 0; h <= hmax_i; ++h) {
+                    P.h = h;
+                    int rest = hmax_i - (m0 - 1);
+                    P.lo0 = std::max(0, h - rest);
+                    P.hi0 = std::min(m0 - 1, h);
+                    long long span = (long long)(P.hi0 - P.lo0 + 1) * (nd == 3 ? m1 : 1) * S;
+                    k_lf_plane<<<(unsigned)((span + 255) / 256), 256, 0, st>>>(P);
+                }
+                k_lf_boundary<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(g, S, fixed, active, tau, dmax);
+            }
+            TRY(cudaGetLastError());
+            TRY(cudaMemcpyAsync(h_dmax.data(), dmax, S * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+            TRY(cudaStreamSynchronize(st));
+            bool changed = false;
+            for (int a = 0; a < S; ++a) {
+                if (!h_active[a]) continue;
+                double dm;
+                std::memcpy(&dm, &h_dmax[a], sizeof dm);
+                if (dm < opts->eik_tol) { h_active[a] = 0; --left; changed = true; }
+            }
+            if (left == 0) { used = cyc; break; }
+            if (changed) TRY(cudaMemcpyAsync(active, h_active.data(), S, cudaMemcpyHostToDevice, st));
+        }
+        k_eik_out<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(SN, T0, tau, T);
+        TRY(cudaGetLastError());
+        TRY(cudaStreamSynchronize(st));
+#undef TRY
+        if (cycles) *cycles = used < 0 ? opts->eik_max_cycles : used;
+        if (used < 0) { set_error("eik_forward_noalloc did not converge in %d cycles", opts->eik_max_cycles); return EIK_ERR_NOT_CONVERGED; }
+        return EIK_OK;
+    } catch (...) {
+        set_error("eik_forward_noalloc failed");
+        return EIK_ERR_INVALID;
+    }
+}

@@ -24,7 +24,8 @@ STATUS = {0: "OK", -1: "INVALID", -2: "OOM", -3: "SINGULAR_BLOCK", -4: "NOT_CONV
 EXPORTED = ["eik_opts_default", "eik_last_error", "eik_version", "eik_forward", "tangent_build", "tangent_apply",
             "tangent_apply_T", "tangent_solve", "tangent_solve_T", "tangent_sample", "tangent_stats", "tangent_dims",
             "tangent_export", "tangent_status", "tangent_free", "sweep_apply", "tangent_debug_hold", "tangent_tune",
-            "lsqr_create", "lsqr_start", "lsqr_iterate", "lsqr_solution", "lsqr_free"]
+            "lsqr_create", "lsqr_start", "lsqr_iterate", "lsqr_solution", "lsqr_free",
+            "eik_forward_noalloc", "eik_forward_noalloc_capacity"]
 
 
 class EikError(RuntimeError):
@@ -67,6 +68,8 @@ def lib():
         L.eik_last_error.restype = C.c_char_p
         L.eik_version.restype = C.c_char_p
         L.eik_forward.argtypes = [C.POINTER(Grid_), P, I, P, P, C.POINTER(Opts), C.POINTER(I), P]
+        L.eik_forward_noalloc.argtypes = [C.POINTER(Grid_), P, I, P, P, C.POINTER(Opts), C.POINTER(I), P]
+        L.eik_forward_noalloc_capacity.restype = C.c_size_t
         L.tangent_build.argtypes = [C.POINTER(Grid_), P, P, I, P, P, I, C.POINTER(Opts), C.POINTER(P), P]
         L.tangent_apply.argtypes = [P, P, I, I, P, P, I, P]
         L.tangent_apply_T.argtypes = [P, P, I, I, P, P, I, P]
@@ -155,6 +158,17 @@ def eik_forward(dgrid: DeviceGrid, s: torch.Tensor, src, opts: Opts | None = Non
     cyc = C.c_int(0)
     _check(lib().eik_forward(C.byref(dgrid.c), _dev(s, torch.float64, "s"), S, C.c_void_p(src.data_ptr()),
                              _dev(out, torch.float64, "T"), C.byref(opts) if opts else None, C.byref(cyc), _stream()))
+    return out, cyc.value
+
+
+def eik_forward_noalloc(dgrid: DeviceGrid, s: torch.Tensor, src, out: torch.Tensor, opts: Opts | None = None):
+    """Same result as eik_forward, without any device allocation inside the library: the
+    caller provides T [S, N] (float64) and the scratch is the library's fixed array."""
+    src = torch.as_tensor(src, dtype=torch.int32).contiguous().cpu()
+    cyc = C.c_int(0)
+    _check(lib().eik_forward_noalloc(C.byref(dgrid.c), _dev(s, torch.float64, "s"), int(src.numel()),
+                                     C.c_void_p(src.data_ptr()), _dev(out, torch.float64, "T"),
+                                     C.byref(opts) if opts else None, C.byref(cyc), _stream()))
     return out, cyc.value
 
 
