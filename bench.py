@@ -145,7 +145,8 @@ def run_ours(args):
             np.save(cache, T.cpu().numpy())
     torch.cuda.synchronize()
     t_state = time.time() - t0
-    opts = eik.default_opts(schedule=eik.SCHED_LEVELS if args.schedule == "levels" else eik.SCHED_PERSISTENT)
+    sched = {"persistent": eik.SCHED_PERSISTENT, "levels": eik.SCHED_LEVELS, "staged": eik.SCHED_STAGED}[args.schedule]
+    opts = eik.default_opts(schedule=sched)
     t0 = time.time()
     tan = eik.Tangent(dg, T, s, src, rec=wl.rec, opts=opts)
     torch.cuda.synchronize()
@@ -259,7 +260,8 @@ def run_ours(args):
     other = "bwd" if dom == "fwd" else "fwd"
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": "k_traverse_persistent<float,4,%s>" % ("false" if dom == "fwd" else "true"),
+                "kernel": {"persistent": "k_traverse_persistent<float,4,%s>", "levels": "k_traverse_level<float,4,%s,1>",
+                           "staged": "k_traverse_staged<float,4,%s>"}[args.schedule] % ("false" if dom == "fwd" else "true"),
                 "bytes_per_launch": ab[dom], "bytes_per_update": round(ab[dom + "_per_update"], 3),
                 "peak_kind": f"{peak_kind} hbm_gbs",
                 "other_direction": {"dir": other, "ms": round(min(mf, mb), 4),
@@ -292,7 +294,7 @@ def run_ours(args):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": upd_step / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * (3 if args.schedule == "persistent" else (2 * max(x["levels"] for x in st) + 1)),
+        "gpu_launches": args.steps * (3 if args.schedule == "persistent" else (2 * max(x["levels"] for x in st) + 3)),
         "clocks": clocks,
         "sweep_baseline": sweep,
         "setup": {"eik_forward_s": round(t_state, 3), "eik_cycles": cyc, "tangent_build_s": round(t_setup, 3),
@@ -434,7 +436,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--schedule", choices=["persistent", "levels"], default="persistent")
+    ap.add_argument("--schedule", choices=["persistent", "levels", "staged"], default="persistent")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-sources", type=int, default=2)

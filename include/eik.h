@@ -56,7 +56,11 @@ typedef enum { EIK_MODEL_SLOWNESS = 0, EIK_MODEL_VELOCITY = 1, EIK_MODEL_RELATIV
 /* Traversal schedule of tangent_apply / tangent_apply_T. */
 typedef enum {
     EIK_SCHED_PERSISTENT = 0,      /* one persistent launch, device level queue, bounded waits */
-    EIK_SCHED_LEVELS = 1           /* one launch per level (host loop, graph-capturable) */
+    EIK_SCHED_LEVELS = 1,          /* one launch per level, replayed from a CUDA graph */
+    EIK_SCHED_STAGED = 2           /* per-level launches whose vector rows are staged in shared
+                                      memory by per-thread async copies (needs R x element size a
+                                      multiple of 16 bytes, >= 64, items x 16-byte lanes <= 512
+                                      and the two stages within 200 KB; else as LEVELS) */
 } eik_schedule;
 
 typedef struct {

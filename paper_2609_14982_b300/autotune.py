@@ -32,6 +32,7 @@ def candidates(R: int, dtype) -> list:
     out = []
     for ch in chunks:
         out.append({"schedule": eik.SCHED_LEVELS, "ctas_per_sm": 0, "rhs_chunk": ch})
+        out.append({"schedule": eik.SCHED_STAGED, "ctas_per_sm": 0, "rhs_chunk": ch})
         for per_sm in (0, 1, 2):
             out.append({"schedule": eik.SCHED_PERSISTENT, "ctas_per_sm": per_sm, "rhs_chunk": ch})
     return out

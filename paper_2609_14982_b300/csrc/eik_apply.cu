@@ -2,10 +2,13 @@
 // (reverse, A^-T) for all sources and right-hand sides (Prop. 3, Sec. 4.3-4.4).
 //
 // Data layout (right-hand-side index fastest):
-//   per-source vectors [S][N][R] in natural node order, so a node's R values are one
-//   contiguous, vector-loadable run; the structure (rows, weights, C*M, receiver slots)
-//   is stored per source in the canonical level order, so one level is a contiguous
-//   slice of every structure array.
+//   the caller's vectors are [S][N][R] (or [N][R]) in natural node order; the
+//   transported field itself (dT or lam) lives in a workspace [S][N][R] in each source's
+//   canonical level order, and rows reference upstream nodes by canonical position.  A
+//   level's results are then one contiguous run of rows, and its gathers read the
+//   contiguous, recently written rows of earlier levels.  The structure (rows, weights,
+//   C*M, receiver slots) is in the same order, so one level is a contiguous slice of
+//   every array.  A natural-order copy of the field is written only when requested.
 // Work: a work item is (source, step, position range) of singleton components of one
 //   level, or one nontrivial SCC block.  Items are ordered step-major across sources.
 //   Persistent schedule: CTAs take items by ticket; an item of step t waits (bounded)
@@ -77,6 +80,7 @@ __device__ __forceinline__ unsigned long long global_ns()
 
 struct TravParams {
     int S, R, n_rec, maxL, nitems;   // R: right-hand sides of this launch (a column chunk)
+    int item_max;                    // positions per singleton item
     long long ld_in, ld_x, ld_aux;   // row strides (elements) of in, x and aux
     long long N;
     int mode;          // MODE_J or MODE_RAW
@@ -92,7 +96,9 @@ struct TravParams {
     const double *cq64;
     const int *rec_slot;
     const void *in;        // forward: p / q ; transpose: y / r
-    void *x;               // dT or lam [S][N][R]
+    void *x;               // dT or lam workspace [S][N][R], canonical order
+    void *out;             // optional natural-order copy of x [S][N][R]
+    long long ld_out;
     void *aux;             // forward: d_rec [S][n_rec][R]; transpose (no sum): g [S][N][R]
     const int4 *items;
     const int2 *ebeg;      // per item: staged edge range
@@ -183,12 +189,13 @@ __device__ __forceinline__ Pack<T, V> node_input(const TravParams &P, int a, int
 }
 
 template <typename T, int V, bool TR>
-__device__ __forceinline__ void node_output(const TravParams &P, int a, int v, int rec, T c, int r, T *x,
+__device__ __forceinline__ void node_output(const TravParams &P, int a, int v, int pos, int rec, T c, int r, T *x,
                                             const Pack<T, V> &acc)
 {
     const long long N = P.N;
     T *aux = reinterpret_cast<T *>(P.aux);
-    store<T, V>(x + (long long)v * P.ld_x + r, acc);
+    store<T, V>(x + (long long)pos * P.ld_x + r, acc);
+    if (P.out) store<T, V>(reinterpret_cast<T *>(P.out) + ((long long)a * N + v) * P.ld_out + r, acc);
     if (P.mode == MODE_J && aux) {
         if (!TR) {
             if (rec >= 0) store<T, V>(aux + ((long long)a * P.n_rec + rec) * P.ld_aux + r, acc);
@@ -202,7 +209,7 @@ __device__ __forceinline__ void node_output(const TravParams &P, int a, int v, i
 }
 
 template <typename T, int V, bool TR, int NPS>
-__device__ __forceinline__ void run_singletons(const TravParams &P, const Stage<T> &sm, int a, int np, int G)
+__device__ __forceinline__ void run_singletons(const TravParams &P, const Stage<T> &sm, int a, int p0, int np, int G)
 {
     const int lane = threadIdx.x % G, slot = threadIdx.x / G, nslot = blockDim.x / G;
     const long long N = P.N;
@@ -239,8 +246,8 @@ __device__ __forceinline__ void run_singletons(const TravParams &P, const Stage<
                     for (int u = 0; u < V; ++u) a1.v[u] += w * x1[e].v[u];
                 }
             }
-            if (on0) node_output<T, V, TR>(P, a, v0, rec0, cq0, r, x, a0);
-            if (on1) node_output<T, V, TR>(P, a, v1, rec1, cq1, r, x, a1);
+            if (on0) node_output<T, V, TR>(P, a, v0, p0 + k0, rec0, cq0, r, x, a0);
+            if (on1) node_output<T, V, TR>(P, a, v1, p0 + k1, rec1, cq1, r, x, a1);
         }
     }
 }
@@ -327,7 +334,8 @@ __device__ void run_block(const TravParams &P, int a, int b)
         const int p = p0 + m;
         const int v = ~perm[p];
         const double val = W[(long long)m * R + r];
-        x[(long long)v * P.ld_x + r] = (T)val;
+        x[(long long)p * P.ld_x + r] = (T)val;
+        if (P.out) reinterpret_cast<T *>(P.out)[((long long)a * N + v) * P.ld_out + r] = (T)val;
         if (P.mode == MODE_J && aux) {
             const int rec = P.rec_slot[a * N + p];
             if (!TR) {
@@ -345,7 +353,7 @@ __device__ __forceinline__ void run_item(const TravParams &P, Stage<T> &sm, int4
     if (it.z >= 0) {
         stage_item<T>(P, sm, it.x, it.z, it.w, eb);
         __syncthreads();
-        run_singletons<T, V, TR, 2>(P, sm, it.x, it.w - it.z, G);
+        run_singletons<T, V, TR, 2>(P, sm, it.x, it.z, it.w - it.z, G);
     } else {
         run_block<T, TR>(P, it.x, ~it.z);
     }
@@ -356,45 +364,55 @@ __device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddep
 
 // ---------------------------------------------------------------- persistent schedule
 template <typename T, int V, bool TR>
-__global__ void __launch_bounds__(256) k_traverse_persistent(TravParams P, int G)
+__global__ void __launch_bounds__(256, 4) k_traverse_persistent(TravParams P, int G)
 {
     __shared__ Stage<T> sm;
-    __shared__ int s_item;
-    __shared__ int s_ok;
+    __shared__ int s_item, s_next, s_ok;
     __shared__ int2 s_eb;
+    if (threadIdx.x == 0) s_item = atomicAdd(P.ticket, 1);
+    __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(P.ticket, 1);
-        __syncthreads();
         const int i = s_item;
         if (i >= P.nitems) break;
         const int4 it = P.items[i];
         if (threadIdx.x == 0) {
             s_eb = P.ebeg[i];
+            s_next = atomicAdd(P.ticket, 1);   // this CTA's tickets stay in increasing order
+        }
+        __syncthreads();
+        // the structure never changes during a traversal: stage it before the wait
+        if (it.z >= 0) stage_item<T>(P, sm, it.x, it.z, it.w, s_eb);
+        if (threadIdx.x == 0) {
             int ok = 1;
             if (it.y > 0) {
                 const int *flag = P.done + (long long)it.x * P.maxL + it.y - 1;
                 const int need = P.item_cnt[(long long)it.x * P.maxL + it.y - 1];
-                const unsigned long long t0 = global_ns();
-                while (ld_acquire(flag) < need) {
-                    if (*(volatile int *)P.err != 0) { ok = 0; break; }
-                    if (global_ns() - t0 > P.timeout_ns) {
-                        if (atomicCAS(P.err, 0, DEV_TIMEOUT) == 0) { P.err[1] = it.x; P.err[2] = it.y; P.err[3] = i; }
-                        ok = 0;
-                        break;
+                if (ld_acquire(flag) < need) {
+                    const unsigned long long t0 = global_ns();
+                    while (ld_acquire(flag) < need) {
+                        if (*(volatile int *)P.err != 0) { ok = 0; break; }
+                        if (global_ns() - t0 > P.timeout_ns) {
+                            if (atomicCAS(P.err, 0, DEV_TIMEOUT) == 0) { P.err[1] = it.x; P.err[2] = it.y; P.err[3] = i; }
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(32);
                     }
-                    __nanosleep(32);
                 }
             }
             s_ok = ok;
         }
         __syncthreads();
         if (!s_ok) break;
-        run_item<T, V, TR>(P, sm, it, s_eb, G);
+        if (it.z >= 0) run_singletons<T, V, TR, 1>(P, sm, it.x, it.z, it.w - it.z, G);
+        else run_block<T, TR>(P, it.x, ~it.z);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
             atomicAdd(P.done + (long long)it.x * P.maxL + it.y, 1);
+            s_item = s_next;
         }
+        __syncthreads();
     }
 }
 
@@ -406,7 +424,7 @@ __global__ void __launch_bounds__(256) k_traverse_persistent(TravParams P, int G
 // is complete and visible.  Parameters are read from device memory, so a captured
 // sequence of these launches does not depend on the caller's buffers.
 template <typename T, int V, bool TR, int NPS>
-__global__ void __launch_bounds__(512) k_traverse_level(const TravParams *__restrict__ Pd, int G, int first)
+__global__ void __launch_bounds__(256, 4) k_traverse_level(const TravParams *__restrict__ Pd, int G, int first)
 {
     __shared__ Stage<T> sm;
     const TravParams &P = *Pd;
@@ -417,7 +435,7 @@ __global__ void __launch_bounds__(512) k_traverse_level(const TravParams *__rest
         stage_item<T>(P, sm, it.x, it.z, it.w, P.ebeg[i]);
         grid_dependency_wait();
         __syncthreads();
-        run_singletons<T, V, TR, NPS>(P, sm, it.x, it.w - it.z, G);
+        run_singletons<T, V, TR, NPS>(P, sm, it.x, it.z, it.w - it.z, G);
     } else {
         grid_dependency_wait();
         run_block<T, TR>(P, it.x, ~it.z);
@@ -426,6 +444,140 @@ __global__ void __launch_bounds__(512) k_traverse_level(const TravParams *__rest
 
 __global__ void k_set_params(TravParams *Pd, TravParams P) { *Pd = P; }
 
+// ---------------------------------------------------------------- staged (async-copy) schedule
+// One launch per step; each CTA walks the step's items with two pipeline stages.  A CTA
+// has item_max x G threads: thread (k, lane) owns position k of the item and the lane's
+// 16-byte column chunk.  For an item it copies, with cp.async, its chunk of the
+// position's input row and of every upstream row into shared memory; it later reads
+// back only what it copied itself, so the copies need no barrier, hold no registers
+// while in flight, and two items per CTA are in flight at once.  While one item
+// computes, the next item's structure is staged and its copies are issued.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+struct StagedMeta {
+    int a, kind, np, ne, block, p0;   // source; 1 singleton range / 0 block; positions; edges; block; first position
+};
+
+template <typename T>
+__device__ __forceinline__ void staged_structure(const TravParams &P, Stage<T> &sm, StagedMeta &meta, int i)
+{
+    const int4 it = P.items[i];
+    if (it.z < 0) {
+        if (threadIdx.x == 0) { meta.a = it.x; meta.kind = 0; meta.np = 0; meta.ne = 0; meta.block = ~it.z; }
+        return;
+    }
+    const int2 eb = P.ebeg[i];
+    stage_item<T>(P, sm, it.x, it.z, it.w, eb);
+    if (threadIdx.x == 0) { meta.a = it.x; meta.kind = 1; meta.np = it.w - it.z; meta.ne = eb.y - eb.x; meta.block = -1; meta.p0 = it.z; }
+}
+
+// rows of a stage, each ROWB bytes: position k's input row at k, edge e's upstream row
+// at item_max + e; this thread copies its 16-byte chunks (column r) of its own position
+template <typename T, bool TR>
+__device__ __forceinline__ void staged_issue(const TravParams &P, const Stage<T> &sm, const StagedMeta &meta,
+                                             unsigned char *rows, int G)
+{
+    const int k = threadIdx.x / G, lane = threadIdx.x % G;
+    if (!meta.kind || k >= meta.np) return;
+    const int v = sm.perm[k];
+    if (v < 0) return;
+    constexpr int V = 16 / sizeof(T);
+    const int R = P.R;
+    const size_t rowb = (size_t)R * sizeof(T);
+    const long long a = meta.a;
+    const T *in = reinterpret_cast<const T *>(P.in);
+    const T *x = reinterpret_cast<const T *>(P.x) + a * P.N * P.ld_x;
+    const T *src_in = nullptr;
+    if (!TR) src_in = in + ((P.mode == MODE_J && P.shared_in ? 0 : a * P.N) + v) * P.ld_in;
+    else if (P.mode == MODE_J) src_in = sm.rec[k] >= 0 ? in + (a * P.n_rec + sm.rec[k]) * P.ld_in : nullptr;
+    else src_in = in + (a * P.N + v) * P.ld_in;
+    const int e0 = sm.rp[k], cnt = sm.rp[k + 1] - e0;
+    for (int r = lane * V; r < R; r += G * V) {
+        if (src_in) cp_async16(rows + (size_t)k * rowb + r * sizeof(T), src_in + r);
+        for (int e = 0; e < cnt; ++e)
+            cp_async16(rows + (size_t)(P.item_max + e0 + e) * rowb + r * sizeof(T), x + (long long)sm.en[e0 + e] * P.ld_x + r);
+    }
+}
+
+template <typename T, bool TR>
+__device__ __forceinline__ void staged_compute(const TravParams &P, const Stage<T> &sm, const StagedMeta &meta,
+                                               const unsigned char *rows, int G)
+{
+    const int k = threadIdx.x / G, lane = threadIdx.x % G;
+    if (k >= meta.np) return;
+    const int v = sm.perm[k];
+    if (v < 0) return;
+    constexpr int V = 16 / sizeof(T);
+    const int R = P.R;
+    const size_t rowb = (size_t)R * sizeof(T);
+    T *x = reinterpret_cast<T *>(P.x) + meta.a * P.N * P.ld_x;
+    const int e0 = sm.rp[k], cnt = sm.rp[k + 1] - e0;
+    const int rec = sm.rec[k];
+    const T c = sm.cq[k];
+    const bool has_in = !(TR && P.mode == MODE_J && rec < 0);
+    const T scale = (!TR && P.mode == MODE_J) ? c : T(1);
+    for (int r = lane * V; r < R; r += G * V) {
+        Pack<T, V> acc;
+        if (has_in) {
+            Pack<T, V> q = *reinterpret_cast<const Pack<T, V> *>(rows + (size_t)k * rowb + r * sizeof(T));
+#pragma unroll
+            for (int u = 0; u < V; ++u) acc.v[u] = scale * q.v[u];
+        } else {
+#pragma unroll
+            for (int u = 0; u < V; ++u) acc.v[u] = T(0);
+        }
+        for (int e = 0; e < cnt; ++e) {
+            const T w = sm.ew[e0 + e];
+            Pack<T, V> xv = *reinterpret_cast<const Pack<T, V> *>(rows + (size_t)(P.item_max + e0 + e) * rowb + r * sizeof(T));
+#pragma unroll
+            for (int u = 0; u < V; ++u) acc.v[u] += w * xv.v[u];
+        }
+        node_output<T, V, TR>(P, meta.a, v, meta.p0 + k, rec, c, r, x, acc);
+    }
+}
+
+template <typename T, bool TR>
+__global__ void __launch_bounds__(512) k_traverse_staged(const TravParams *__restrict__ Pd, int G, int first, int n)
+{
+    extern __shared__ __align__(128) unsigned char dyn[];
+    __shared__ Stage<T> sm[2];
+    __shared__ StagedMeta meta[2];
+    const TravParams &P = *Pd;
+    const size_t stage_bytes = (size_t)P.item_max * (1 + MAX_ROW) * P.R * sizeof(T);
+    grid_dependents_launch();
+    int idx = blockIdx.x;
+    if (idx >= n) return;
+    staged_structure<T>(P, sm[0], meta[0], first + idx);
+    grid_dependency_wait();          // rows of earlier levels are complete and visible
+    __syncthreads();
+    staged_issue<T, TR>(P, sm[0], meta[0], dyn, G);
+    cp_async_commit();
+    for (int j = 0;; ++j) {
+        const int buf = j & 1;
+        const int nxt = idx + gridDim.x;
+        if (nxt < n) {
+            staged_structure<T>(P, sm[buf ^ 1], meta[buf ^ 1], first + nxt);
+            __syncthreads();
+            staged_issue<T, TR>(P, sm[buf ^ 1], meta[buf ^ 1], dyn + (buf ^ 1) * stage_bytes, G);
+        }
+        cp_async_commit();           // (possibly empty) group of the next item
+        cp_async_wait<1>();          // this thread's copies of the current item have landed
+        if (meta[buf].kind) staged_compute<T, TR>(P, sm[buf], meta[buf], dyn + buf * stage_bytes, G);
+        else run_block<T, TR>(P, meta[buf].a, meta[buf].block);
+        __syncthreads();             // structure of this stage is reused two items later
+        if (nxt >= n) break;
+        idx = nxt;
+    }
+    cp_async_wait<0>();
+}
+
 // g[j][r] = sum_a cq_a[j] lam_a[j][r] in source order.  FP64 path: FP64 products and
 // sum.  FP32 path: FP32 products with a compensated (Kahan) FP32 sum, so the rounding
 // error does not grow with the number of sources (B300's FP64 rate would make an FP64
@@ -433,20 +585,21 @@ __global__ void k_set_params(TravParams *Pd, TravParams P) { *Pd = P; }
 constexpr int SUMB = 8;
 
 template <typename T>
-__global__ void k_source_sum(long long N, int S, int R, const T *__restrict__ cqn, const T *__restrict__ lam,
-                             long long ld_lam, T *__restrict__ g, long long ld_g)
+__global__ void k_source_sum(long long N, int S, int R, const T *__restrict__ cqn, const int *__restrict__ pos,
+                             const T *__restrict__ lam, long long ld_lam, T *__restrict__ g, long long ld_g)
 {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= N * R) return;
     long long j = t / R;
     int r = (int)(t - j * R);
-    long long idx = j * ld_lam + r;
     T acc = 0, comp = 0;
     for (int a0 = 0; a0 < S; a0 += SUMB) {
         T vals[SUMB];
 #pragma unroll
         for (int b = 0; b < SUMB; ++b)
-            vals[b] = a0 + b < S ? __ldg(cqn + (long long)(a0 + b) * N + j) * __ldcs(lam + (long long)(a0 + b) * N * ld_lam + idx) : T(0);
+            vals[b] = a0 + b < S ? __ldg(cqn + (long long)(a0 + b) * N + j) *
+                                       __ldcs(lam + ((long long)(a0 + b) * N + __ldg(pos + (long long)(a0 + b) * N + j)) * ld_lam + r)
+                                 : T(0);
 #pragma unroll
         for (int b = 0; b < SUMB; ++b) {
             if (sizeof(T) == 8) {
@@ -521,12 +674,72 @@ static int launch_levels(Tangent *t, int G, int threads, int first_step, TravPar
 }
 
 template <typename T, int V, bool TR>
+static int launch_staged(Tangent *t, int G, int threads, size_t dyn, int per_sm, TravParams *Pd, cudaStream_t st)
+{
+    const std::vector<int> &sp = TR ? t->step_ptr_bwd : t->step_ptr_fwd;
+    const int cap = t->num_sms * per_sm;
+    for (int s = 0; s < t->maxL; ++s) {
+        int n = sp[s + 1] - sp[s];
+        if (n <= 0) continue;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)std::min(n, cap));
+        cfg.blockDim = dim3((unsigned)threads);
+        cfg.dynamicSmemBytes = dyn;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = s == 0 ? 0 : 1;
+        EIK_CHECK(cudaLaunchKernelEx(&cfg, k_traverse_staged<T, TR>, (const TravParams *)Pd, G, sp[s], n));
+    }
+    return EIK_OK;
+}
+
+template <typename T, int V, bool TR>
 static int launch_traverse(Tangent *t, TravParams &P, int G, cudaStream_t st)
 {
-    if (t->opts.schedule == EIK_SCHED_LEVELS) {
-        // one item per CTA, one node per slot (two when a CTA would exceed 512 threads)
-        const bool two = ITEM_MAX * G > 512;
-        const int threads = std::max(32, two ? ITEM_MAX * G / 2 : ITEM_MAX * G);
+    const size_t rowb = (size_t)P.R * sizeof(T);
+    const bool staged_ok = rowb % 16 == 0 && rowb >= 64 && (P.ld_in * sizeof(T)) % 16 == 0 &&
+                           (P.ld_x * sizeof(T)) % 16 == 0 && V * sizeof(T) == 16;
+    const size_t staged_dyn = 2 * (size_t)t->item_max * (1 + MAX_ROW) * rowb;
+    if (t->opts.schedule == EIK_SCHED_STAGED && staged_ok && t->item_max * G <= 512 && staged_dyn <= 200 * 1024) {
+        // one thread per (position, 16-byte lane); rows wider than 32 lanes loop over columns
+        const int threads = std::max(32, t->item_max * G);
+        const size_t dyn = staged_dyn;
+        EIK_CHECK(cudaFuncSetAttribute(k_traverse_staged<T, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        int per_sm = 0;
+        EIK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_staged<T, TR>, threads, dyn));
+        per_sm = std::max(per_sm, 1);
+        if (!t->params_d) EIK_CHECK(cudaMalloc(&t->params_d, 2 * sizeof(TravParams)));
+        TravParams *Pd = t->params_d + (TR ? 1 : 0);
+        k_set_params<<<1, 1, 0, st>>>(Pd, P);
+        EIK_CHECK_LAUNCH();
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        EIK_CHECK(cudaStreamIsCapturing(st, &cs));
+        if (cs != cudaStreamCaptureStatusNone || !t->opts_graph)
+            return launch_staged<T, V, TR>(t, G, threads, dyn, per_sm, Pd, st);
+        const long long key = (1ll << 50) | ((long long)TR << 40) | ((long long)sizeof(T) << 32) | ((long long)P.R << 8) | G;
+        cudaGraphExec_t &exec = t->level_graphs[key];
+        if (!exec) {
+            if (!t->cap_stream) EIK_CHECK(cudaStreamCreateWithFlags(&t->cap_stream, cudaStreamNonBlocking));
+            EIK_CHECK(cudaStreamBeginCapture(t->cap_stream, cudaStreamCaptureModeThreadLocal));
+            int rc = launch_staged<T, V, TR>(t, G, threads, dyn, per_sm, Pd, t->cap_stream);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(t->cap_stream, &g);
+            if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+            e = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) { exec = nullptr; return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__); }
+        }
+        EIK_CHECK(cudaGraphLaunch(exec, st));
+        return EIK_OK;
+    }
+    if (t->opts.schedule == EIK_SCHED_LEVELS || t->opts.schedule == EIK_SCHED_STAGED) {
+        // one item per CTA; slots of G lanes, one node in flight per slot
+        const bool two = false;
+        const int threads = std::min(256, std::max(32, t->item_max * G));
         if (!t->params_d) EIK_CHECK(cudaMalloc(&t->params_d, 2 * sizeof(TravParams)));
         TravParams *Pd = t->params_d + (TR ? 1 : 0);
         k_set_params<<<1, 1, 0, st>>>(Pd, P);
@@ -556,8 +769,8 @@ static int launch_traverse(Tangent *t, TravParams &P, int G, cudaStream_t st)
         EIK_CHECK(cudaGraphLaunch(exec, st));
         return EIK_OK;
     }
-    // persistent: a CTA holds ITEM_MAX / 2 node slots of G lanes (two nodes per slot)
-    const int threads = std::min(256, std::max(32, ITEM_MAX * G / 2));
+    // persistent: slots of G lanes, one node in flight per slot, at most 256 threads
+    const int threads = std::min(256, std::max(32, t->item_max * G));
     int per_sm = t->opts.ctas_per_sm;
     if (per_sm <= 0) {
         EIK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_persistent<T, V, TR>, threads, 0));
@@ -577,7 +790,9 @@ static int dispatch_v(Tangent *t, TravParams &P, cudaStream_t st)
 {
     // widest vector that divides R and keeps every row 16-byte aligned when possible
     const int R = P.R;
-    auto fits = [&](int v) { return R % v == 0 && P.ld_in % v == 0 && P.ld_x % v == 0 && P.ld_aux % v == 0; };
+    auto fits = [&](int v) {
+        return R % v == 0 && P.ld_in % v == 0 && P.ld_x % v == 0 && P.ld_aux % v == 0 && P.ld_out % v == 0;
+    };
     int V = 1;
     if (sizeof(T) == 4 && fits(4)) V = 4;
     else if (fits(2)) V = 2;
@@ -613,17 +828,21 @@ int traverse(Tangent *t, bool TR, int mode, const void *in, int shared_in, int R
         const int unit = dtype == EIK_F32 ? 4 : 2;
         if (R % unit == 0) Rc = std::max(unit, Rc / unit * unit);
     }
-    size_t need_vec = out_full ? 0 : (size_t)t->S * t->N * Rc * esz;
+    // the transported field always lives in the canonical-order workspace
+    size_t need_vec = (size_t)t->S * t->N * Rc * esz;
     int rc = ensure_workspace(t, need_vec, (size_t)t->ws_rows * Rc);
     if (rc) return rc;
     for (int r0 = 0; r0 < R; r0 += Rc) {
         const int w = std::min(Rc, R - r0);
         const char *inp = static_cast<const char *>(in) + r0 * esz;
-        char *xp = out_full ? static_cast<char *>(out_full) + r0 * esz : static_cast<char *>(t->ws_vec);
+        char *xp = static_cast<char *>(t->ws_vec);
+        char *outp = out_full ? static_cast<char *>(out_full) + r0 * esz : nullptr;
         char *auxp = out_aux ? static_cast<char *>(out_aux) + r0 * esz : nullptr;
         TravParams P{};
         P.S = t->S; P.R = w; P.n_rec = t->n_rec; P.maxL = t->maxL; P.nitems = t->nitems; P.N = t->N;
-        P.ld_in = R; P.ld_x = out_full ? R : w; P.ld_aux = R;
+        P.item_max = t->item_max;
+        P.ld_in = R; P.ld_x = w; P.ld_aux = R; P.ld_out = R;
+        P.out = outp;
         P.mode = mode; P.shared_in = shared_in; P.sum = sum_sources;
         P.perm = t->perm;
         P.rowptr = TR ? t->cptr : t->rowptr;
@@ -648,10 +867,10 @@ int traverse(Tangent *t, bool TR, int mode, const void *in, int shared_in, int R
             long long n = t->N * w;
             unsigned blocks = (unsigned)((n + 255) / 256);
             if (dtype == EIK_F32)
-                k_source_sum<float><<<blocks, 256, 0, st>>>(t->N, t->S, w, t->cqn32, (const float *)xp, P.ld_x,
+                k_source_sum<float><<<blocks, 256, 0, st>>>(t->N, t->S, w, t->cqn32, t->pos, (const float *)xp, P.ld_x,
                                                             (float *)auxp, (long long)R);
             else
-                k_source_sum<double><<<blocks, 256, 0, st>>>(t->N, t->S, w, t->cqn64, (const double *)xp, P.ld_x,
+                k_source_sum<double><<<blocks, 256, 0, st>>>(t->N, t->S, w, t->cqn64, t->pos, (const double *)xp, P.ld_x,
                                                              (double *)auxp, (long long)R);
             EIK_CHECK_LAUNCH();
         }

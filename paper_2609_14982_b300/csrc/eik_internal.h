@@ -24,8 +24,9 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
 
 #define EIK_CHECK_LAUNCH() EIK_CHECK(cudaGetLastError())
 
-// Largest singleton range of one work item (positions staged in shared memory).
-constexpr int ITEM_MAX = 32;
+// Capacity of one work item (positions staged in shared memory); the build option
+// eik_opts.chunk picks the item size actually used (default: the capacity).
+constexpr int ITEM_MAX = 64;
 
 // Device-side fault codes latched in Tangent::err (first one wins).
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_SINGULAR = 2, DEV_BAD_INDEX = 3 };
@@ -77,11 +78,11 @@ struct Tangent {
     int *label = nullptr;     // [S][N] natural: SCC id (smallest local node)
     int *level = nullptr;     // [S][N] natural: level of the node's component
     int *rowptr = nullptr;    // [S][N+1] local offsets into the forward edge arrays
-    int *up_node = nullptr;   // [E] upstream node j (natural index)
+    int *up_node = nullptr;   // [E] canonical position of upstream node j
     float *up_w32 = nullptr;
     double *up_w64 = nullptr;
     int *cptr = nullptr;      // [S][N+1] local offsets into the transposed edge arrays
-    int *dn_node = nullptr;   // [E'] downstream node i (natural index)
+    int *dn_node = nullptr;   // [E'] canonical position of downstream node i
     float *dn_w32 = nullptr;
     double *dn_w64 = nullptr;
     double *cq64 = nullptr;   // [S][N] C*M coefficient per position
@@ -104,6 +105,7 @@ struct Tangent {
     long long lu_words = 0, piv_words = 0, ws_rows = 0;
     // work items of the traversals: {src, step, p0, p1} or {src, step, ~blk, 0}
     int nitems = 0;
+    int item_max = 0;             // positions per singleton item of this tangent
     int4 *items_fwd = nullptr;
     int4 *items_bwd = nullptr;
     int2 *ebeg_fwd = nullptr;     // per item: [first, last) local edge offsets of its rows

@@ -466,7 +466,7 @@ __global__ void k_counts(GridDesc g, long long SN, const int *__restrict__ perm,
     tcnt[p] = tc;
 }
 
-__global__ void k_fill(GridDesc g, long long SN, const int *__restrict__ perm, const int *__restrict__ label,
+__global__ void k_fill(GridDesc g, long long SN, const int *__restrict__ perm, const int *__restrict__ pos, const int *__restrict__ label,
                        const int *__restrict__ cnt, const int *__restrict__ nnode, const double *__restrict__ nw,
                        const unsigned char *__restrict__ upmask, const long long *__restrict__ fscan,
                        const long long *__restrict__ tscan, const long long *__restrict__ fbase,
@@ -492,7 +492,7 @@ __global__ void k_fill(GridDesc g, long long SN, const int *__restrict__ perm, c
         long long u = a * g.N + j;
         if (member && label[u] == label[v]) continue;
         double w = nw[v * slots + e];
-        up_node[fo] = j;
+        up_node[fo] = pos[u];            // the traversal's workspace is in canonical order
         up_w64[fo] = w;
         up_w32[fo] = (float)w;
         ++fo;
@@ -503,7 +503,7 @@ __global__ void k_fill(GridDesc g, long long SN, const int *__restrict__ perm, c
         double w = 0.0;
         for (int e = 0; e < cnt[u]; ++e)
             if (nnode[u * slots + e] == self) w = nw[u * slots + e];
-        dn_node[to] = (int)(u - a * g.N);
+        dn_node[to] = pos[u];
         dn_w64[to] = w;
         dn_w32[to] = (float)w;
         ++to;
@@ -969,7 +969,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
     TRY(dalloc(&t->dn_node, ht[S]));
     TRY(dalloc(&t->dn_w32, ht[S]));
     TRY(dalloc(&t->dn_w64, ht[S]));
-    k_fill<<<blocks_for(SN), 256, 0, st>>>(g, SN, t->perm, lab, cnt, t->nrow_node, t->nrow_w, upmask, fscan, tscan,
+    k_fill<<<blocks_for(SN), 256, 0, st>>>(g, SN, t->perm, t->pos, lab, cnt, t->nrow_node, t->nrow_w, upmask, fscan, tscan,
                                            fbase_d, tbase_d, t->rowptr, t->cptr, t->up_node, t->up_w32, t->up_w64,
                                            t->dn_node, t->dn_w32, t->dn_w64);
     TRY(cudaGetLastError());
@@ -1069,6 +1069,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
     // ---- traversal work items: level-major over sources
     {
         int chunk = opts->chunk > 0 ? std::min(opts->chunk, ITEM_MAX) : ITEM_MAX;
+        t->item_max = chunk;
         std::vector<std::vector<int4>> per((size_t)S * maxL);
         std::vector<int> blk_ptr(S + 1, 0);
         // blocks are ordered by (source, position), hence by (source, level)

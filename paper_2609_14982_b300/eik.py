@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libeik.so")
 
 EIK_F64, EIK_F32 = 0, 1
 MODEL_SLOWNESS, MODEL_VELOCITY, MODEL_RELATIVE = 0, 1, 2
-SCHED_PERSISTENT, SCHED_LEVELS = 0, 1
+SCHED_PERSISTENT, SCHED_LEVELS, SCHED_STAGED = 0, 1, 2
 STATUS = {0: "OK", -1: "INVALID", -2: "OOM", -3: "SINGULAR_BLOCK", -4: "NOT_CONVERGED", -5: "TIMEOUT",
           -6: "CUDA", -7: "CYCLE"}
 

@@ -132,13 +132,15 @@ def test_solve_primal_and_transpose(oracle_mod, built, name, dtype, R):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_levels_schedule_matches_persistent(built, dtype):
-    """The per-level schedule (graph-replayed launches) and the persistent schedule run
-    the same arithmetic per node; they may differ only in how the compiler fuses
-    multiply-adds."""
+@pytest.mark.parametrize("sched", [eik.SCHED_LEVELS, eik.SCHED_STAGED])
+@pytest.mark.parametrize("R", [8, 64])
+def test_levels_schedule_matches_persistent(built, dtype, sched, R):
+    """The per-level schedules (graph-replayed launches, with rows in registers or staged
+    in shared memory by bulk copies) and the persistent schedule run the same arithmetic
+    per node; they may differ only in how the compiler fuses multiply-adds."""
     g, Ts, s, srcs, otans, tan = built("table3-41x41x25")
-    tan_l = built("table3-41x41x25", opts=eik.default_opts(schedule=eik.SCHED_LEVELS))[-1]
-    q = torch.randn((len(srcs), g.N, 8), device=DEV, dtype=dtype, generator=torch.Generator(DEV).manual_seed(5))
+    tan_l = built("table3-41x41x25", opts=eik.default_opts(schedule=sched, chunk=16))[-1]
+    q = torch.randn((len(srcs), g.N, R), device=DEV, dtype=dtype, generator=torch.Generator(DEV).manual_seed(5))
     tol = 1e-6 if dtype == torch.float32 else 1e-14
     for _ in range(2):                       # the second call replays the captured graph
         for f in ("solve", "solve_T"):
@@ -147,7 +149,7 @@ def test_levels_schedule_matches_persistent(built, dtype):
     tan_l.status()
 
 
-@pytest.mark.parametrize("schedule", [eik.SCHED_PERSISTENT, eik.SCHED_LEVELS])
+@pytest.mark.parametrize("schedule", [eik.SCHED_PERSISTENT, eik.SCHED_LEVELS, eik.SCHED_STAGED])
 def test_rhs_chunking_and_tune(built, schedule):
     """Right-hand sides processed in column chunks (and options changed on a built
     tangent) give the same results as one pass."""
@@ -159,7 +161,7 @@ def test_rhs_chunking_and_tune(built, schedule):
     tan_r.tune(schedule=schedule, rhs_chunk=0)
     _, ref = tan_r.apply(p, shared_model=True)
     gref, _ = tan_r.apply_T(y, sum_sources=True)
-    for chunk in (4, 8, 12):
+    for chunk in (4, 8, 16):
         tan_r.tune(rhs_chunk=chunk)
         _, got = tan_r.apply(p, shared_model=True)
         gg, _ = tan_r.apply_T(y, sum_sources=True)
@@ -309,3 +311,22 @@ def test_autotuner_applies_a_setting_and_keeps_results(built, tmp_path):
     assert float((got - ref).abs().max()) <= 1e-6 * float(ref.abs().max())
     again = autotune(tan, 8, torch.float32, cache_path=cache)
     assert again["cached"] is True and again["setting"] == rec["setting"]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_staged_schedule_jacobian_against_oracle(oracle_mod, dtype):
+    """J p and J^T y with the staged (bulk-copy) schedule against the oracle, R = 64."""
+    g, Ts, s, srcs, rec = _config1_case()
+    _, G, _ = oracle_mod.metric(g)
+    otans = [oracle_mod.build_tangent(g, G, Ts[a], s, int(srcs[a])) for a in range(len(srcs))]
+    tan = eik.Tangent(eik.DeviceGrid(g), torch.tensor(Ts, device=DEV), torch.tensor(s, device=DEV), srcs,
+                      rec=rec, opts=eik.default_opts(schedule=eik.SCHED_STAGED, chunk=16))
+    rng = np.random.default_rng(12)
+    p = torch.tensor(rng.standard_normal((g.N, 64)), device=DEV, dtype=dtype)
+    y = torch.tensor(rng.standard_normal((len(srcs), len(rec), 64)), device=DEV, dtype=dtype)
+    for _ in range(2):
+        _, drec = tan.apply(p, shared_model=True)
+        gs, _ = tan.apply_T(y, sum_sources=True)
+    tan.status()
+    assert rel_err(drec.cpu(), oracle_mod.J(otans, s, rec, p.double().cpu().numpy())) <= TOL[dtype]
+    assert rel_err(gs.cpu(), oracle_mod.JT(otans, s, rec, y.double().cpu().numpy())) <= TOL[dtype]
