@@ -87,6 +87,26 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def measured_traffic(direction: str) -> float | None:
+    """DRAM bytes per node-update of the traversal kernel from the committed ncu summary
+    (profiles/traffic.txt: one line per direction with the SHA-256 of the kernel source
+    it was captured from); None once the kernel source has changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_2609_14982_b300", "csrc", "eik_apply.cu")
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        for line in open(path):
+            if line.startswith("#") or not line.strip():
+                continue
+            kv = dict(tok.split("=", 1) for tok in line.split())
+            if kv.get("direction") == direction and kv.get("source_sha256") == digest:
+                return float(kv["bytes_per_update"])
+    except (OSError, ValueError, KeyError):
+        return None
+    return None
+
+
 def algorithmic_bytes(st_list, R: int, esz: int, S: int, N: int, n_rec: int) -> dict:
     """Bytes each call must move with this layout (per call, all sources):
     structure per (source, node): perm 4 + row offset 4 + C*M 4 + receiver slot 4 and
@@ -258,8 +278,9 @@ def run_ours(args):
     dom_ms = max(mf, mb)
     achieved = ab[dom] / (dom_ms / 1e3) / 1e9
     other = "bwd" if dom == "fwd" else "fwd"
+    tpu = measured_traffic(dom) if args.schedule == "persistent" else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4), "traffic": None if tpu is None else round(tpu * ab["updates"]),
                 "kernel": {"persistent": "k_traverse_persistent<float,4,%s>", "levels": "k_traverse_level<float,4,%s,1>",
                            "staged": "k_traverse_staged<float,4,%s>"}[args.schedule] % ("false" if dom == "fwd" else "true"),
                 "bytes_per_launch": ab[dom], "bytes_per_update": round(ab[dom + "_per_update"], 3),
@@ -325,7 +346,8 @@ def run_lsqr(args):
     dg = eik.DeviceGrid(g)
     s = torch.tensor(wl.s, device="cuda")
     t0 = time.time()
-    T, cyc = eik.eik_forward(dg, s, src)
+    # setup only: the state solve uses FP32 arithmetic away from the sources
+    T, cyc = eik.eik_forward(dg, s, src, opts=eik.default_opts(eik_fp32=1))
     torch.cuda.synchronize()
     t_state = time.time() - t0
     t0 = time.time()

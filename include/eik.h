@@ -88,6 +88,12 @@ typedef struct {
     /* traversal */
     int rhs_chunk;             /* process right-hand sides in column chunks of this many
                                   (0 = all at once); bounds the internal workspace */
+    /* eik_forward precision split */
+    int eik_fp32;              /* 1: nodes farther than eik_fp64_radius * max(dxi) from the
+                                  source update in FP32 arithmetic (FP64 storage), the source
+                                  neighbourhood stays FP64; the stop test then uses
+                                  max(eik_tol, 1e-6).  0 (default): FP64 everywhere */
+    double eik_fp64_radius;    /* (default 8) */
 } eik_opts;
 
 typedef struct {

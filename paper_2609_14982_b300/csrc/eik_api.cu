@@ -38,6 +38,8 @@ void eik_opts_default(eik_opts *o)
     o->sweep_tol = 1e-12;
     o->sweep_max_cycles = 10000;
     o->rhs_chunk = 0;
+    o->eik_fp32 = 0;
+    o->eik_fp64_radius = 8.0;
 }
 
 const char *eik_last_error(void) { return eik::last_error(); }

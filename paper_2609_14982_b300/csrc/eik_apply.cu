@@ -108,8 +108,7 @@ struct TravParams {
     int *err;              // {code, source, step, item}
     const int4 *blk_desc;
     const long long *blk_off;
-    const double *lu;
-    const int *piv;
+    const double *binv;    // block inverses
     double *ws;
     unsigned long long timeout_ns;
 };
@@ -253,15 +252,18 @@ __device__ __forceinline__ void run_singletons(const TravParams &P, const Stage<
 }
 
 // ---------------------------------------------------------------- block items
-// FP64 solve of one nontrivial SCC block for all right-hand sides (Sec. 4.3):
-// forward: b = q_C + W_ext x_ext, then P, L, U; transpose: b = r_C + W_ext^T lam_ext,
-// then U^T, L^T, P^T.  Right-hand sides are independent, one thread each.
+// FP64 solve of one nontrivial SCC block for all right-hand sides (Sec. 4.3).  The
+// right-hand side gathers the block's external rows: forward b = q_C + W_ext x_ext,
+// transpose b = r_C + W_ext^T lam_ext.  The solve multiplies by A_C^-1, formed once at
+// build time from the partial-pivot factors P A_C = L U (the transpose reads the same
+// matrix transposed, A_C^-T = (A_C^-1)^T), so each (row, right-hand side) is one
+// independent dot product instead of a k-step triangular sweep.
 template <typename T, bool TR>
 __device__ void run_block(const TravParams &P, int a, int b)
 {
     const int4 d = P.blk_desc[b];
     const int p0 = d.y, k = d.z;
-    const long long luo = P.blk_off[3 * b], pvo = P.blk_off[3 * b + 1], wso = P.blk_off[3 * b + 2];
+    const long long luo = P.blk_off[3 * b], wso = P.blk_off[3 * b + 2];
     const int R = P.R;
     const long long N = P.N;
     const int *perm = P.perm + a * N;
@@ -273,8 +275,7 @@ __device__ void run_block(const TravParams &P, int a, int b)
     T *x = reinterpret_cast<T *>(P.x) + a * N * P.ld_x;
     T *aux = reinterpret_cast<T *>(P.aux);
     double *W = P.ws + wso * R;
-    const double *LU = P.lu + luo;
-    const int *pv = P.piv + pvo;
+    const double *Ainv = P.binv + luo;
     for (long long idx = threadIdx.x; idx < (long long)k * R; idx += blockDim.x) {
         const int m = (int)(idx / R), r = (int)(idx % R);
         const int p = p0 + m;
@@ -294,46 +295,17 @@ __device__ void run_block(const TravParams &P, int a, int b)
         W[(long long)m * R + r] = acc;
     }
     __syncthreads();
-    for (int r = threadIdx.x; r < R; r += blockDim.x) {
-        double *bcol = W + r;
-        if (!TR) {
-            for (int m = 0; m < k; ++m) {
-                int q = pv[m];
-                if (q != m) { double t = bcol[(long long)m * R]; bcol[(long long)m * R] = bcol[(long long)q * R]; bcol[(long long)q * R] = t; }
-            }
-            for (int m = 0; m < k; ++m) {
-                double acc = bcol[(long long)m * R];
-                for (int c = 0; c < m; ++c) acc -= LU[(long long)m * k + c] * bcol[(long long)c * R];
-                bcol[(long long)m * R] = acc;
-            }
-            for (int m = k - 1; m >= 0; --m) {
-                double acc = bcol[(long long)m * R];
-                for (int c = m + 1; c < k; ++c) acc -= LU[(long long)m * k + c] * bcol[(long long)c * R];
-                bcol[(long long)m * R] = acc / LU[(long long)m * k + m];
-            }
-        } else {
-            for (int m = 0; m < k; ++m) {
-                double acc = bcol[(long long)m * R];
-                for (int c = 0; c < m; ++c) acc -= LU[(long long)c * k + m] * bcol[(long long)c * R];
-                bcol[(long long)m * R] = acc / LU[(long long)m * k + m];
-            }
-            for (int m = k - 1; m >= 0; --m) {
-                double acc = bcol[(long long)m * R];
-                for (int c = m + 1; c < k; ++c) acc -= LU[(long long)c * k + m] * bcol[(long long)c * R];
-                bcol[(long long)m * R] = acc;
-            }
-            for (int m = k - 1; m >= 0; --m) {
-                int q = pv[m];
-                if (q != m) { double t = bcol[(long long)m * R]; bcol[(long long)m * R] = bcol[(long long)q * R]; bcol[(long long)q * R] = t; }
-            }
-        }
-    }
-    __syncthreads();
     for (long long idx = threadIdx.x; idx < (long long)k * R; idx += blockDim.x) {
         const int m = (int)(idx / R), r = (int)(idx % R);
+        double val = 0.0;
+        if (!TR) {
+            const double *row = Ainv + (long long)m * k;
+            for (int c = 0; c < k; ++c) val += row[c] * W[(long long)c * R + r];
+        } else {
+            for (int c = 0; c < k; ++c) val += Ainv[(long long)c * k + m] * W[(long long)c * R + r];
+        }
         const int p = p0 + m;
         const int v = ~perm[p];
-        const double val = W[(long long)m * R + r];
         x[(long long)p * P.ld_x + r] = (T)val;
         if (P.out) reinterpret_cast<T *>(P.out)[((long long)a * N + v) * P.ld_out + r] = (T)val;
         if (P.mode == MODE_J && aux) {
@@ -858,7 +830,7 @@ int traverse(Tangent *t, bool TR, int mode, const void *in, int shared_in, int R
         P.ebeg = TR ? t->ebeg_bwd : t->ebeg_fwd;
         P.item_cnt = t->item_cnt + (TR ? (size_t)t->S * t->maxL : 0);
         P.done = t->done; P.ticket = t->ticket; P.err = t->err;
-        P.blk_desc = t->blk_desc; P.blk_off = t->blk_off; P.lu = t->lu; P.piv = t->piv; P.ws = t->ws_blk;
+        P.blk_desc = t->blk_desc; P.blk_off = t->blk_off; P.binv = t->binv; P.ws = t->ws_blk;
         P.timeout_ns = (unsigned long long)(t->opts.wait_timeout_s * 1e9);
         if (dtype == EIK_F32) rc = TR ? dispatch_v<float, true>(t, P, st) : dispatch_v<float, false>(t, P, st);
         else rc = TR ? dispatch_v<double, true>(t, P, st) : dispatch_v<double, false>(t, P, st);

@@ -58,6 +58,8 @@ __global__ void k_eik_prep(GridDesc g, int S, const double *__restrict__ xyz, co
 struct LFParams {
     GridDesc g;
     int S, order, h, lo0, hi0;
+    int fp32;                  // update nodes with T0 > t0_fp64 in FP32 arithmetic
+    const double *t0_fp64;     // [S] threshold on T0 per source (s_src * radius)
     const double *G, *s, *T0, *g0, *alpha;
     const unsigned char *fixed;
     const unsigned char *active;   // [S] sources still iterating
@@ -93,6 +95,34 @@ __device__ __forceinline__ double lf_update(const LFParams &P, long long a, long
     return num / den;
 }
 
+// the same update in FP32 arithmetic (inputs rounded to FP32, result stored as FP64)
+__device__ __forceinline__ double lf_update_f32(const LFParams &P, long long a, long long i)
+{
+    const GridDesc &g = P.g;
+    const int nd = g.ndim;
+    const long long v = a * g.N + i;
+    const double *tau = P.tau + a * g.N;
+    const float T0 = (float)P.T0[v];
+    const float ti = (float)tau[i];
+    float p[3], Pv[3];
+    for (int d = 0; d < nd; ++d)
+        p[d] = ((float)tau[i + g.st[d]] - (float)tau[i - g.st[d]]) / (2.0f * (float)g.dxi[d]);
+    for (int b = 0; b < nd; ++b) Pv[b] = ti * (float)P.g0[v * nd + b] + T0 * p[b];
+    float H2 = 0.0f;
+    for (int x = 0; x < nd; ++x) {
+        float row = 0.0f;
+        for (int b = 0; b < nd; ++b) row = row + (float)P.G[i * nd * nd + x * nd + b] * Pv[b];
+        H2 = H2 + Pv[x] * row;
+    }
+    float num = (float)P.s[i] - sqrtf(H2), den = 0.0f;
+    for (int d = 0; d < nd; ++d) {
+        const float al = (float)P.alpha[v * nd + d];
+        num = num + al * ((float)tau[i + g.st[d]] + (float)tau[i - g.st[d]]) / (2.0f * (float)g.dxi[d]);
+        den = den + al / (float)g.dxi[d];
+    }
+    return (double)(num / den);
+}
+
 __global__ void k_lf_plane(LFParams P)
 {
     const GridDesc &g = P.g;
@@ -123,7 +153,7 @@ __global__ void k_lf_plane(LFParams P)
     long long v = a * g.N + i;
     if (P.fixed[v]) return;
     int c[3] = {i0, i1, i2};
-    double nv = lf_update(P, a, i, c);
+    double nv = (P.fp32 && P.T0[v] > P.t0_fp64[a]) ? lf_update_f32(P, a, i) : lf_update(P, a, i, c);
     double old = P.tau[v];
     P.tau[v] = nv;
     double dd = fabs(nv - old);
@@ -152,6 +182,13 @@ __global__ void k_lf_boundary(GridDesc g, int S, const unsigned char *__restrict
     double dd = fabs(nv - ta[i]);
     ta[i] = nv;
     atomicMax(dmax + a, (unsigned long long)__double_as_longlong(dd));
+}
+
+// T0 beyond which a node of source a is far enough from it for FP32 arithmetic
+__global__ void k_t0_threshold(int S, const double *__restrict__ s, const int *__restrict__ src, double dist, double *out)
+{
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < S) out[a] = s[src[a]] * dist;
 }
 
 __global__ void k_eik_out(long long SN, const double *T0, const double *tau, double *T)
@@ -187,9 +224,10 @@ extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const in
         unsigned char *fixed = nullptr, *active = nullptr;
         int *src_d = nullptr;
         unsigned long long *dmax = nullptr;
+        double *t0_fp64 = nullptr;
         auto release = [&]() {
             cudaFree(G); cudaFree(Jm); cudaFree(T0); cudaFree(g0); cudaFree(alpha); cudaFree(tau);
-            cudaFree(fixed); cudaFree(active); cudaFree(src_d); cudaFree(dmax);
+            cudaFree(fixed); cudaFree(active); cudaFree(src_d); cudaFree(dmax); cudaFree(t0_fp64);
         };
 #define TRY(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { int rc_ = cuda_fail(e_, #call, __FILE__, __LINE__); release(); return rc_; } } while (0)
         TRY(cudaMalloc(&G, N * nd * nd * sizeof(double)));
@@ -202,6 +240,7 @@ extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const in
         TRY(cudaMalloc(&src_d, S * sizeof(int)));
         TRY(cudaMalloc(&dmax, S * sizeof(unsigned long long)));
         TRY(cudaMalloc(&active, S));
+        TRY(cudaMalloc(&t0_fp64, S * sizeof(double)));
         TRY(cudaMemcpyAsync(src_d, src_node, S * sizeof(int), cudaMemcpyHostToDevice, st));
         double hmax = 0.0;
         for (int d = 0; d < nd; ++d) hmax = std::max(hmax, g.dxi[d]);
@@ -212,6 +251,9 @@ extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const in
         LFParams P{};
         P.g = g; P.S = S; P.G = G; P.s = s; P.T0 = T0; P.g0 = g0; P.alpha = alpha; P.fixed = fixed; P.tau = tau;
         P.dmax = dmax; P.active = active;
+        P.fp32 = opts->eik_fp32 ? 1 : 0; P.t0_fp64 = t0_fp64;
+        k_t0_threshold<<<(S + 127) / 128, 128, 0, st>>>(S, s, src_d, opts->eik_fp64_radius * hmax, t0_fp64);
+        const double tol = opts->eik_fp32 ? std::max(opts->eik_tol, 1e-6) : opts->eik_tol;
         const int m0 = g.n[0] - 2, m1 = g.n[1] - 2, m2 = nd == 3 ? g.n[2] - 2 : 1;
         const int hmax_i = (m0 - 1) + (m1 - 1) + (nd == 3 ? m2 - 1 : 0);
         const int nord = 1 << nd;
@@ -242,9 +284,10 @@ extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const in
                 if (!h_active[a]) continue;
                 double dm;
                 std::memcpy(&dm, &h_dmax[a], sizeof dm);
-                if (dm < opts->eik_tol) { h_active[a] = 0; --left; changed = true; }
+                if (dm < tol) { h_active[a] = 0; --left; changed = true; }
             }
             if (left == 0) { used = cyc; break; }
+            (void)0;
             if (changed) TRY(cudaMemcpyAsync(active, h_active.data(), S, cudaMemcpyHostToDevice, st));
         }
         k_eik_out<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(SN, T0, tau, T);
@@ -296,6 +339,7 @@ size_t noalloc_bytes(int nd, long long N, int S)
     b += align256((size_t)S * sizeof(int));                  // source nodes
     b += align256((size_t)S * sizeof(unsigned long long));   // max change per source
     b += align256((size_t)S);                                // active flags
+    b += align256((size_t)S * sizeof(double));               // FP32 thresholds
     return b;
 }
 
@@ -358,6 +402,7 @@ extern "C" int eik_forward_noalloc(const eik_grid *gin, const double *s, int S, 
         int *src_d = (int *)carve((size_t)S * sizeof(int));
         unsigned long long *dmax = (unsigned long long *)carve((size_t)S * sizeof(unsigned long long));
         unsigned char *active = carve((size_t)S);
+        double *t0_fp64 = (double *)carve((size_t)S * sizeof(double));
         cudaStream_t st = (cudaStream_t)stream;
 #define TRY(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return cuda_fail(e_, #call, __FILE__, __LINE__); } while (0)
         TRY(cudaMemcpyAsync(src_d, src_node, S * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -372,6 +417,9 @@ extern "C" int eik_forward_noalloc(const eik_grid *gin, const double *s, int S, 
         LFParams P{};
         P.g = g; P.S = S; P.G = G; P.s = s; P.T0 = T0; P.g0 = g0; P.alpha = alpha; P.fixed = fixed; P.tau = tau;
         P.dmax = dmax; P.active = active;
+        P.fp32 = opts->eik_fp32 ? 1 : 0; P.t0_fp64 = t0_fp64;
+        k_t0_threshold<<<(S + 127) / 128, 128, 0, st>>>(S, s, src_d, opts->eik_fp64_radius * hmax, t0_fp64);
+        const double tol = opts->eik_fp32 ? std::max(opts->eik_tol, 1e-6) : opts->eik_tol;
         const int m0 = g.n[0] - 2, m1 = g.n[1] - 2, m2 = nd == 3 ? g.n[2] - 2 : 1;
         const int hmax_i = (m0 - 1) + (m1 - 1) + (nd == 3 ? m2 - 1 : 0);
         const int nord = 1 << nd;
@@ -402,9 +450,10 @@ extern "C" int eik_forward_noalloc(const eik_grid *gin, const double *s, int S, 
                 if (!h_active[a]) continue;
                 double dm;
                 std::memcpy(&dm, &h_dmax[a], sizeof dm);
-                if (dm < opts->eik_tol) { h_active[a] = 0; --left; changed = true; }
+                if (dm < tol) { h_active[a] = 0; --left; changed = true; }
             }
             if (left == 0) { used = cyc; break; }
+            (void)0;
             if (changed) TRY(cudaMemcpyAsync(active, h_active.data(), S, cudaMemcpyHostToDevice, st));
         }
         k_eik_out<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(SN, T0, tau, T);

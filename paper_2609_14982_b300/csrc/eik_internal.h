@@ -100,7 +100,8 @@ struct Tangent {
     int nblk = 0;
     int4 *blk_desc = nullptr;     // {src, p0, k, level}
     long long *blk_off = nullptr; // [nblk][3] {lu, piv, ws}
-    double *lu = nullptr;
+    double *lu = nullptr;         // P A_C = L U factors of every nontrivial block
+    double *binv = nullptr;       // A_C^-1 of every block, row-major, same offsets as lu
     int *piv = nullptr;
     long long lu_words = 0, piv_words = 0, ws_rows = 0;
     // work items of the traversals: {src, step, p0, p1} or {src, step, ~blk, 0}

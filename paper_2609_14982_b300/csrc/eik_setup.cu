@@ -682,6 +682,40 @@ __global__ void k_item_edges(int n, long long N, const int4 *items, const int *r
     eb[i] = make_int2(rp[it.z], rp[it.w]);
 }
 
+// A_C^-1 from the factors P A_C = L U: column c of the inverse solves A_C x = e_c
+// (row swaps, then L, then U), one column per thread, written in place into column c of
+// the row-major k x k result.
+__global__ void k_block_inverse(const int4 *__restrict__ desc, const long long *__restrict__ off,
+                                const double *__restrict__ lu, const int *__restrict__ piv, double *inv)
+{
+    int b = blockIdx.x;
+    int k = desc[b].z;
+    const double *LU = lu + off[3 * b + 0];
+    const int *P = piv + off[3 * b + 1];
+    double *X = inv + off[3 * b + 0];
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        for (int m = 0; m < k; ++m) X[(long long)m * k + c] = m == c ? 1.0 : 0.0;
+        for (int m = 0; m < k; ++m) {
+            int q = P[m];
+            if (q != m) {
+                double t = X[(long long)m * k + c];
+                X[(long long)m * k + c] = X[(long long)q * k + c];
+                X[(long long)q * k + c] = t;
+            }
+        }
+        for (int m = 0; m < k; ++m) {
+            double acc = X[(long long)m * k + c];
+            for (int j = 0; j < m; ++j) acc -= LU[(long long)m * k + j] * X[(long long)j * k + c];
+            X[(long long)m * k + c] = acc;
+        }
+        for (int m = k - 1; m >= 0; --m) {
+            double acc = X[(long long)m * k + c];
+            for (int j = m + 1; j < k; ++j) acc -= LU[(long long)m * k + j] * X[(long long)j * k + c];
+            X[(long long)m * k + c] = acc / LU[(long long)m * k + m];
+        }
+    }
+}
+
 __global__ void k_compact_heads(long long SN, const int *head, const int *scan, int *hpos)
 {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -729,7 +763,7 @@ void free_tangent(Tangent *t)
     void *ptrs[] = {t->perm, t->pos, t->label, t->level, t->rowptr, t->up_node, t->up_w32, t->up_w64, t->cptr,
                     t->dn_node, t->dn_w32, t->dn_w64, t->cq64, t->cq32, t->cqn64, t->cqn32, t->rec_slot,
                     t->rec_nat, t->nrow_cnt, t->nrow_node, t->nrow_w, t->cs_nat, t->blk_desc, t->blk_off, t->lu,
-                    t->piv, t->items_fwd, t->items_bwd, t->ebeg_fwd, t->ebeg_bwd, t->item_cnt, t->done, t->ticket, t->err, t->ws_vec,
+                    t->binv, t->piv, t->items_fwd, t->items_bwd, t->ebeg_fwd, t->ebeg_bwd, t->item_cnt, t->done, t->ticket, t->err, t->ws_vec,
                     t->ws_blk, t->ebase_d, t->tbase_d};
     for (void *p : ptrs) if (p) cudaFree(p);
     if (t->params_d) cudaFree((void *)t->params_d);
@@ -1049,6 +1083,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
         TRY(dalloc(&t->blk_desc, std::max(nb, 1)));
         TRY(dalloc(&t->blk_off, 3 * std::max(nb, 1)));
         TRY(dalloc(&t->lu, std::max(lo, 1ll)));
+        TRY(dalloc(&t->binv, std::max(lo, 1ll)));
         TRY(dalloc(&t->piv, std::max(po, 1ll)));
         TRY(dalloc(&t->err, 4));
         TRY(cudaMemsetAsync(t->err, 0, 4 * sizeof(int), st));
@@ -1058,6 +1093,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
             k_block_fill<<<nb, 256, 0, st>>>(g, t->blk_desc, t->blk_off, t->perm, t->pos, lab, cnt, t->nrow_node,
                                              t->nrow_w, t->lu);
             k_block_lu<<<nb, 256, 0, st>>>(t->blk_desc, t->blk_off, t->lu, t->piv, opts->lu_pivot_tol, t->err);
+            k_block_inverse<<<nb, 128, 0, st>>>(t->blk_desc, t->blk_off, t->lu, t->piv, t->binv);
             TRY(cudaGetLastError());
             int e = 0;
             TRY(cudaMemcpyAsync(&e, t->err, sizeof(int), cudaMemcpyDeviceToHost, st));

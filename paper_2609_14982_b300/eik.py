@@ -42,7 +42,8 @@ class Opts(C.Structure):
     _fields_ = [("model", C.c_int), ("lu_pivot_tol", C.c_double), ("schedule", C.c_int), ("threads", C.c_int),
                 ("chunk", C.c_int), ("ctas_per_sm", C.c_int), ("wait_timeout_s", C.c_double),
                 ("eik_tol", C.c_double), ("eik_max_cycles", C.c_int), ("eik_src_radius", C.c_double),
-                ("sweep_tol", C.c_double), ("sweep_max_cycles", C.c_int), ("rhs_chunk", C.c_int)]
+                ("sweep_tol", C.c_double), ("sweep_max_cycles", C.c_int), ("rhs_chunk", C.c_int),
+                ("eik_fp32", C.c_int), ("eik_fp64_radius", C.c_double)]
 
 
 class Stats(C.Structure):

@@ -266,6 +266,27 @@ def test_eik_forward_matches_oracle(oracle_mod):
         assert rel_err(T3[a].cpu(), ref) <= 1e-12
 
 
+def test_eik_forward_fp32_far_field(oracle_mod):
+    """Precision split of the state solve: FP32 arithmetic away from the source, FP64 in
+    its neighbourhood; the result stays within 1e-5 of the FP64 oracle state."""
+    wl = W.config1()
+    g = wl.grid
+    srcs = [int(wl.src[0]), g.index(40, 0)]
+    T, cyc = eik.eik_forward(eik.DeviceGrid(g), torch.tensor(wl.s, device=DEV), srcs,
+                             opts=eik.default_opts(eik_fp32=1))
+    for a, k in enumerate(srcs):
+        ref, _ = oracle_mod.eik_forward(g, wl.s, k)
+        assert rel_err(T[a].cpu(), ref) <= 1e-5
+    g3, _ = W._config3d("3d", (41, 41, 21), 20.0, 8.0, 2.0, 20263)
+    s3 = 1.0 / W._velocity3d(g3, 2.0)
+    srcs3 = [g3.index(10, 10, 0), g3.index(30, 20, 0)]
+    T3, _ = eik.eik_forward(eik.DeviceGrid(g3), torch.tensor(s3, device=DEV), srcs3,
+                            opts=eik.default_opts(eik_fp32=1))
+    for a, k in enumerate(srcs3):
+        ref, _ = oracle_mod.eik_forward(g3, s3, k)
+        assert rel_err(T3[a].cpu(), ref) <= 1e-5
+
+
 def test_eik_forward_homogeneous_exact():
     """In a homogeneous medium tau = 1 is the discrete fixed point: T = s |x - x_s|."""
     g = W.table1_grid(21)
