@@ -87,10 +87,11 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def measured_traffic(direction: str) -> float | None:
+def measured_traffic(direction: str, kernel: str) -> float | None:
     """DRAM bytes per node-update of the traversal kernel from the committed ncu summary
-    (profiles/traffic.txt: one line per direction with the SHA-256 of the kernel source
-    it was captured from); None once the kernel source has changed since the capture."""
+    (profiles/traffic.txt: one line per kernel and direction with the SHA-256 of the
+    kernel source it was captured from); None once the kernel source has changed since
+    the capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     src = os.path.join(ROOT, "paper_2609_14982_b300", "csrc", "eik_apply.cu")
@@ -100,7 +101,7 @@ def measured_traffic(direction: str) -> float | None:
             if line.startswith("#") or not line.strip():
                 continue
             kv = dict(tok.split("=", 1) for tok in line.split())
-            if kv.get("direction") == direction and kv.get("source_sha256") == digest:
+            if kv.get("direction") == direction and kv.get("kernel") == kernel and kv.get("source_sha256") == digest:
                 return float(kv["bytes_per_update"])
     except (OSError, ValueError, KeyError):
         return None
@@ -166,7 +167,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_state = time.time() - t0
     sched = {"persistent": eik.SCHED_PERSISTENT, "levels": eik.SCHED_LEVELS, "staged": eik.SCHED_STAGED}[args.schedule]
-    opts = eik.default_opts(schedule=sched)
+    opts = eik.default_opts(schedule=sched, item_deps=0 if args.level_waits else 1, ctas_per_sm=args.ctas_per_sm)
     t0 = time.time()
     tan = eik.Tangent(dg, T, s, src, rec=wl.rec, opts=opts)
     torch.cuda.synchronize()
@@ -278,11 +279,13 @@ def run_ours(args):
     dom_ms = max(mf, mb)
     achieved = ab[dom] / (dom_ms / 1e3) / 1e9
     other = "bwd" if dom == "fwd" else "fwd"
-    tpu = measured_traffic(dom) if args.schedule == "persistent" else None
+    kname = {"persistent": "k_traverse_persistent<float,4,%s>", "levels": "k_traverse_level<float,4,%s,1>",
+             "staged": "k_traverse_staged<float,4,%s>"}[args.schedule]
+    kname = kname % ("false" if dom == "fwd" else "true")
+    tpu = measured_traffic(dom, kname)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None if tpu is None else round(tpu * ab["updates"]),
-                "kernel": {"persistent": "k_traverse_persistent<float,4,%s>", "levels": "k_traverse_level<float,4,%s,1>",
-                           "staged": "k_traverse_staged<float,4,%s>"}[args.schedule] % ("false" if dom == "fwd" else "true"),
+                "kernel": kname,
                 "bytes_per_launch": ab[dom], "bytes_per_update": round(ab[dom + "_per_update"], 3),
                 "peak_kind": f"{peak_kind} hbm_gbs",
                 "other_direction": {"dir": other, "ms": round(min(mf, mb), 4),
@@ -310,7 +313,7 @@ def run_ours(args):
         "data": "synthetic (seeded recipe of the 3-D tomography-scale config; no public dataset)",
         "config": {"workload": workload, "grid": list(g.n), "nodes": N, "sources_per_gpu": S, "rhs": R,
                    "receivers": n_rec, "precision": "FP32 substitution, FP64 SCC blocks",
-                   "schedule": args.schedule, "l2": "inputs larger than L2 (dT/lam 3.3 GB per direction)",
+                   "schedule": args.schedule, "waits": "levels" if args.level_waits else "items", "l2": "inputs larger than L2 (dT/lam 3.3 GB per direction)",
                    "parallelism": f"source-sharded x{world}" if world > 1 else "single GPU"},
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -459,6 +462,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--schedule", choices=["persistent", "levels", "staged"], default="persistent")
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--level-waits", action="store_true",
+                    help="persistent items wait for their whole previous level, not only their upstream items")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-sources", type=int, default=2)

@@ -94,6 +94,10 @@ typedef struct {
                                   neighbourhood stays FP64; the stop test then uses
                                   max(eik_tol, 1e-6).  0 (default): FP64 everywhere */
     double eik_fp64_radius;    /* (default 8) */
+    /* persistent schedule */
+    int item_deps;             /* 1 (default): a work item waits only for the items holding its
+                                  upstream rows; 0: for every item of its source's previous
+                                  level (the plain level barrier) */
 } eik_opts;
 
 typedef struct {
@@ -252,7 +256,8 @@ int tangent_status(eik_tangent *t, eik_stream stream);
 
 /*
  * tangent_tune -- replace the run-time options of a built tangent: schedule, ctas_per_sm,
- * rhs_chunk and wait_timeout_s are taken from opts (structure options are ignored).
+ * rhs_chunk, wait_timeout_s and item_deps are taken from opts (structure options are
+ * ignored).
  * Used by the autotuner; affects later calls only.
  */
 int tangent_tune(eik_tangent *t, const eik_opts *opts);
@@ -260,7 +265,8 @@ int tangent_tune(eik_tangent *t, const eik_opts *opts);
 /*
  * tangent_debug_hold -- test hook for the bounded device-side waits of the persistent
  * schedule.  Raises by one the number of completed items the forward traversal waits
- * for before (source, step), so that wait can never be satisfied: the next persistent
+ * for before (source, step), so that wait can never be satisfied, and makes every item
+ * wait for its whole previous level while a hold is in place: the next persistent
  * tangent_apply / tangent_solve ends after about wait_timeout_s and tangent_status
  * returns EIK_ERR_TIMEOUT.  source < 0 undoes every hold.  No fault is raised on the
  * device; the context stays usable.

@@ -2,8 +2,9 @@
 
 The structure of a tangent is fixed at build time; how it is traversed is not.  This
 module times one J p and one J^T y (CUDA events on the current stream) for each
-candidate run-time setting -- schedule (persistent level queue or graph-replayed
-per-level launches), right-hand-side chunk, persistent CTAs per SM -- applies the
+candidate run-time setting -- schedule (persistent item queue or graph-replayed
+per-level launches), right-hand-side chunk, persistent CTAs per SM, per-item or
+per-level waits -- applies the
 fastest with tangent_tune and caches the choice per (grid size, sources, levels, R,
 dtype) in a JSON file.
 """
@@ -34,7 +35,9 @@ def candidates(R: int, dtype) -> list:
         out.append({"schedule": eik.SCHED_LEVELS, "ctas_per_sm": 0, "rhs_chunk": ch})
         out.append({"schedule": eik.SCHED_STAGED, "ctas_per_sm": 0, "rhs_chunk": ch})
         for per_sm in (0, 1, 2):
-            out.append({"schedule": eik.SCHED_PERSISTENT, "ctas_per_sm": per_sm, "rhs_chunk": ch})
+            for deps in (1, 0):
+                out.append({"schedule": eik.SCHED_PERSISTENT, "ctas_per_sm": per_sm, "rhs_chunk": ch,
+                            "item_deps": deps})
     return out
 
 

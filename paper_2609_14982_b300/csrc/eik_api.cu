@@ -40,6 +40,7 @@ void eik_opts_default(eik_opts *o)
     o->rhs_chunk = 0;
     o->eik_fp32 = 0;
     o->eik_fp64_radius = 8.0;
+    o->item_deps = 1;
 }
 
 const char *eik_last_error(void) { return eik::last_error(); }
@@ -213,6 +214,7 @@ int tangent_tune(eik_tangent *tt, const eik_opts *o)
     t->opts.ctas_per_sm = o->ctas_per_sm;
     t->opts.rhs_chunk = o->rhs_chunk;
     t->opts.wait_timeout_s = o->wait_timeout_s;
+    t->opts.item_deps = o->item_deps;
     return EIK_OK;
 }
 

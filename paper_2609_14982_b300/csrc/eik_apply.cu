@@ -11,9 +11,11 @@
 //   every array.  A natural-order copy of the field is written only when requested.
 // Work: a work item is (source, step, position range) of singleton components of one
 //   level, or one nontrivial SCC block.  Items are ordered step-major across sources.
-//   Persistent schedule: CTAs take items by ticket; an item of step t waits (bounded)
-//   until every item of step t-1 of its own source has completed.  Since tickets are
-//   handed out in order, every item waited on is held by a running CTA: no deadlock.
+//   Persistent schedule: CTAs take items by ticket; an item waits (bounded) only for
+//   the items that hold its upstream positions (recorded at build time; an item with
+//   too many waits for every item of its source's previous step instead).  Every such
+//   item has a lower ticket, and tickets are handed out in order, so every item waited
+//   on is held by a running CTA or done: no deadlock.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -71,6 +73,11 @@ __device__ __forceinline__ int ld_acquire(const int *p)
     return v;
 }
 
+__device__ __forceinline__ void st_release(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ unsigned long long global_ns()
 {
     unsigned long long t;
@@ -104,6 +111,9 @@ struct TravParams {
     const int2 *ebeg;      // per item: staged edge range
     const int *item_cnt;   // [S][maxL] items per (source, step) of this direction
     int *done;             // [S][maxL]
+    const int *deps;       // [nitems][DEP_MAX] items holding this item's upstream positions
+    const int *ndeps;      // [nitems], -1: too many, wait for the whole previous step
+    int *item_done;        // [nitems]
     int *ticket;
     int *err;              // {code, source, step, item}
     const int4 *blk_desc;
@@ -258,8 +268,12 @@ __device__ __forceinline__ void run_singletons(const TravParams &P, const Stage<
 // build time from the partial-pivot factors P A_C = L U (the transpose reads the same
 // matrix transposed, A_C^-T = (A_C^-1)^T), so each (row, right-hand side) is one
 // independent dot product instead of a k-step triangular sweep.
-template <typename T, bool TR>
-__device__ void run_block(const TravParams &P, int a, int b)
+struct CtaSync { __device__ void operator()() const { __syncthreads(); } };
+
+// the solve runs on threads tid = 0 .. nthr-1 of the CTA, which sync() synchronises
+template <typename T, bool TR, typename Sync = CtaSync>
+__device__ void run_block(const TravParams &P, int a, int b, int tid = threadIdx.x, int nthr = blockDim.x,
+                          Sync sync = Sync())
 {
     const int4 d = P.blk_desc[b];
     const int p0 = d.y, k = d.z;
@@ -276,7 +290,7 @@ __device__ void run_block(const TravParams &P, int a, int b)
     T *aux = reinterpret_cast<T *>(P.aux);
     double *W = P.ws + wso * R;
     const double *Ainv = P.binv + luo;
-    for (long long idx = threadIdx.x; idx < (long long)k * R; idx += blockDim.x) {
+    for (long long idx = tid; idx < (long long)k * R; idx += nthr) {
         const int m = (int)(idx / R), r = (int)(idx % R);
         const int p = p0 + m;
         const int v = ~__ldg(perm + p);
@@ -294,8 +308,8 @@ __device__ void run_block(const TravParams &P, int a, int b)
         for (int e = rp[p]; e < rp[p + 1]; ++e) acc += ew[e] * (double)__ldcg(x + (long long)en[e] * P.ld_x + r);
         W[(long long)m * R + r] = acc;
     }
-    __syncthreads();
-    for (long long idx = threadIdx.x; idx < (long long)k * R; idx += blockDim.x) {
+    sync();
+    for (long long idx = tid; idx < (long long)k * R; idx += nthr) {
         const int m = (int)(idx / R), r = (int)(idx % R);
         double val = 0.0;
         if (!TR) {
@@ -333,60 +347,6 @@ __device__ __forceinline__ void run_item(const TravParams &P, Stage<T> &sm, int4
 
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-// ---------------------------------------------------------------- persistent schedule
-template <typename T, int V, bool TR>
-__global__ void __launch_bounds__(256, 4) k_traverse_persistent(TravParams P, int G)
-{
-    __shared__ Stage<T> sm;
-    __shared__ int s_item, s_next, s_ok;
-    __shared__ int2 s_eb;
-    if (threadIdx.x == 0) s_item = atomicAdd(P.ticket, 1);
-    __syncthreads();
-    for (;;) {
-        const int i = s_item;
-        if (i >= P.nitems) break;
-        const int4 it = P.items[i];
-        if (threadIdx.x == 0) {
-            s_eb = P.ebeg[i];
-            s_next = atomicAdd(P.ticket, 1);   // this CTA's tickets stay in increasing order
-        }
-        __syncthreads();
-        // the structure never changes during a traversal: stage it before the wait
-        if (it.z >= 0) stage_item<T>(P, sm, it.x, it.z, it.w, s_eb);
-        if (threadIdx.x == 0) {
-            int ok = 1;
-            if (it.y > 0) {
-                const int *flag = P.done + (long long)it.x * P.maxL + it.y - 1;
-                const int need = P.item_cnt[(long long)it.x * P.maxL + it.y - 1];
-                if (ld_acquire(flag) < need) {
-                    const unsigned long long t0 = global_ns();
-                    while (ld_acquire(flag) < need) {
-                        if (*(volatile int *)P.err != 0) { ok = 0; break; }
-                        if (global_ns() - t0 > P.timeout_ns) {
-                            if (atomicCAS(P.err, 0, DEV_TIMEOUT) == 0) { P.err[1] = it.x; P.err[2] = it.y; P.err[3] = i; }
-                            ok = 0;
-                            break;
-                        }
-                        __nanosleep(32);
-                    }
-                }
-            }
-            s_ok = ok;
-        }
-        __syncthreads();
-        if (!s_ok) break;
-        if (it.z >= 0) run_singletons<T, V, TR, 1>(P, sm, it.x, it.z, it.w - it.z, G);
-        else run_block<T, TR>(P, it.x, ~it.z);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(P.done + (long long)it.x * P.maxL + it.y, 1);
-            s_item = s_next;
-        }
-        __syncthreads();
-    }
-}
 
 // ---------------------------------------------------------------- per-level schedule
 // One launch per step: every CTA runs one item, with no ticket, wait or counter.  The
@@ -550,6 +510,269 @@ __global__ void __launch_bounds__(512) k_traverse_staged(const TravParams *__res
     cp_async_wait<0>();
 }
 
+// ---------------------------------------------------------------- shared-memory item stages
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+template <typename T> __device__ __forceinline__ void cp_async_t(T *dst, const T *src)
+{
+    if (sizeof(T) == 8) cp_async8(dst, src);
+    else cp_async4(dst, src);
+}
+
+template <typename T> struct ItemStage {
+    T cq[ITEM_MAX];
+    T ew[MAX_ROW * ITEM_MAX];
+    int perm[ITEM_MAX];
+    int rec[ITEM_MAX];
+    int rp[ITEM_MAX + 1];        // raw local edge offsets (subtract ebx)
+    int en[MAX_ROW * ITEM_MAX];
+    int deps[DEP_MAX];           // items holding the upstream rows (persistent schedule)
+    int nd;                      // their number; -1: wait for the whole previous level
+    int4 it;                     // item descriptor
+    int idx;                     // ticket; >= nitems ends the compute warps
+    int ebx, eby;                // the item's local edge range
+};
+
+// row of the traversal's input for a position of source a, or nullptr (zero input)
+template <typename T, bool TR>
+__device__ __forceinline__ const T *input_row(const TravParams &P, long long a, int v, int rec)
+{
+    const T *in = reinterpret_cast<const T *>(P.in);
+    if (!TR) return in + ((P.mode == MODE_J && P.shared_in ? 0 : a * P.N) + v) * P.ld_in;
+    if (P.mode == MODE_J) return rec >= 0 ? in + (a * P.n_rec + rec) * P.ld_in : nullptr;
+    return in + (a * P.N + v) * P.ld_in;
+}
+
+template <typename T, int V, bool TR>
+__device__ __forceinline__ void run_stage_singletons(const TravParams &P, const ItemStage<T> &S, const unsigned char *tile,
+                                                int G)
+{
+    const int lane = threadIdx.x % G, slot = threadIdx.x / G, nslot = blockDim.x / G;
+    const long long a = S.it.x;
+    const int p0 = S.it.z, np = S.it.w - S.it.z;
+    const int R = P.R;
+    const size_t rowb = (size_t)R * sizeof(T);
+    T *x = reinterpret_cast<T *>(P.x) + a * P.N * P.ld_x;
+    for (int k = slot; k < np; k += nslot) {
+        const int v = S.perm[k];
+        if (v < 0) continue;      // member of a nontrivial block
+        const int e0 = S.rp[k] - S.ebx, cnt = S.rp[k + 1] - S.rp[k];
+        const int rec = S.rec[k];
+        const T c = S.cq[k];
+        const bool has_in = !(TR && P.mode == MODE_J && rec < 0);
+        const T scale = (!TR && P.mode == MODE_J) ? c : T(1);
+        for (int r = lane * V; r < R; r += G * V) {
+            Pack<T, V> xv[MAX_ROW];
+#pragma unroll
+            for (int e = 0; e < MAX_ROW; ++e)
+                if (e < cnt) xv[e] = load_l2<T, V>(x + (long long)S.en[e0 + e] * P.ld_x + r);
+            Pack<T, V> acc;
+            if (tile) {
+                if (has_in) {
+                    const Pack<T, V> q = *reinterpret_cast<const Pack<T, V> *>(tile + (size_t)k * rowb + r * sizeof(T));
+#pragma unroll
+                    for (int u = 0; u < V; ++u) acc.v[u] = scale * q.v[u];
+                } else {
+#pragma unroll
+                    for (int u = 0; u < V; ++u) acc.v[u] = T(0);
+                }
+            } else {
+                acc = node_input<T, V, TR>(P, (int)a, v, rec, c, r);
+            }
+#pragma unroll
+            for (int e = 0; e < MAX_ROW; ++e)
+                if (e < cnt) {
+                    const T w = S.ew[e0 + e];
+#pragma unroll
+                    for (int u = 0; u < V; ++u) acc.v[u] += w * xv[e].v[u];
+                }
+            node_output<T, V, TR>(P, (int)a, v, p0 + k, rec, c, r, x, acc);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- persistent schedule
+// One launch; CTAs take items by ticket, each CTA in increasing ticket order, and an
+// item waits (bounded) only for lower tickets -- the items holding its upstream rows,
+// or every item of its source's previous level -- so every item waited on is held by a
+// running CTA or done: no deadlock.  Per CTA the work of neighbouring items overlaps:
+//   while item c computes, the structure (and dependency list) of the next item n is
+//   copied into the other shared-memory stage with cp.async and the ticket after n is
+//   taken; after c, n's input rows are copied into shared memory with cp.async while
+//   warp 0 waits for n's dependencies.
+// So between two dependent levels only the wait, the upstream gathers (L2) and the
+// release (one fence) remain.
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ void st_relaxed(int *p, int v)
+{
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// structure of item S.idx (descriptor already in S) into S, by all threads of the CTA
+template <typename T>
+__device__ __forceinline__ void issue_structure(const TravParams &P, ItemStage<T> &S)
+{
+    const int i = S.idx;
+    const int4 it = S.it;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (P.ndeps && it.y > 0) {
+        if (tid < DEP_MAX) cp_async4(&S.deps[tid], P.deps + (long long)i * DEP_MAX + tid);
+        else if (tid == DEP_MAX) cp_async4(&S.nd, P.ndeps + i);
+    }
+    if (it.z < 0) return;
+    const long long N = P.N, a = it.x;
+    const int p0 = it.z, np = it.w - it.z, ne = S.eby - S.ebx;
+    const int *rp = P.rowptr + a * (N + 1) + p0;
+    const long long o = a * N + p0;
+    const T *cq = reinterpret_cast<const T *>(P.cq) + o;
+    for (int k = tid; k <= np; k += nt) {
+        cp_async4(&S.rp[k], rp + k);
+        if (k < np) {
+            cp_async4(&S.perm[k], P.perm + o + k);
+            cp_async4(&S.rec[k], P.rec_slot + o + k);
+            cp_async_t<T>(&S.cq[k], cq + k);
+        }
+    }
+    const long long e0 = P.ebase[a] + S.ebx;
+    const T *ew = reinterpret_cast<const T *>(P.ew) + e0;
+    for (int k = tid; k < ne; k += nt) {
+        cp_async4(&S.en[k], P.enode + e0 + k);
+        cp_async_t<T>(&S.ew[k], ew + k);
+    }
+}
+
+// input rows of item S (structure visible) into the tile, 16 bytes per copy
+template <typename T, bool TR>
+__device__ __forceinline__ void issue_input(const TravParams &P, const ItemStage<T> &S, unsigned char *tile)
+{
+    if (S.it.z < 0) return;
+    const long long a = S.it.x;
+    const int np = S.it.w - S.it.z;
+    const size_t rowb = (size_t)P.R * sizeof(T);
+    const int chunks = (int)(rowb / 16);
+    for (int q = threadIdx.x; q < np * chunks; q += blockDim.x) {
+        const int k = q / chunks, c = q - k * chunks;
+        const int v = S.perm[k];
+        if (v < 0) continue;
+        const T *src = input_row<T, TR>(P, a, v, S.rec[k]);
+        if (src) cp_async16(tile + (size_t)k * rowb + (size_t)c * 16, reinterpret_cast<const unsigned char *>(src) + (size_t)c * 16);
+    }
+}
+
+// descriptor of ticket i into S (one thread)
+template <typename T>
+__device__ __forceinline__ void load_desc(const TravParams &P, ItemStage<T> &S, int i)
+{
+    S.idx = i;
+    if (i < P.nitems) {
+        S.it = P.items[i];
+        const int2 eb = P.ebeg[i];
+        S.ebx = eb.x;
+        S.eby = eb.y;
+    }
+    S.nd = -1;
+}
+
+template <typename T, int V, bool TR>
+__global__ void __launch_bounds__(256, 4) k_traverse_persistent(TravParams P, int G, int tile_bytes)
+{
+    extern __shared__ __align__(128) unsigned char dyn[];
+    __shared__ ItemStage<T> stg[2];
+    __shared__ int s_ok;
+    const int tid = threadIdx.x;
+    const int nitems = P.nitems;
+    const unsigned FULL = 0xffffffffu;
+    if (tid == 0) {
+        load_desc(P, stg[0], atomicAdd(P.ticket, 1));
+        stg[1].idx = atomicAdd(P.ticket, 1);
+    }
+    __syncthreads();
+    if (stg[0].idx >= nitems) return;
+    issue_structure<T>(P, stg[0]);
+    cp_async_commit();
+    if (tid == 0) load_desc(P, stg[1], stg[1].idx);
+    cp_async_wait<0>();
+    __syncthreads();
+    if (tile_bytes) issue_input<T, TR>(P, stg[0], dyn);
+    cp_async_commit();
+    for (int b = 0;; b ^= 1) {
+        ItemStage<T> &C = stg[b];
+        ItemStage<T> &Nx = stg[b ^ 1];
+        const int4 it = C.it;
+        const int i = C.idx;
+        // ---- wait (warp 0) for the items holding the upstream rows
+        if (tid < 32) {
+            int ok = 1;
+            if (it.y > 0) {
+                const int nd = C.nd;
+                const int *flag = nullptr;
+                int need = 1;
+                if (nd < 0) {
+                    if (tid == 0) {
+                        flag = P.done + (long long)it.x * P.maxL + it.y - 1;
+                        need = P.item_cnt[(long long)it.x * P.maxL + it.y - 1];
+                    }
+                } else if (tid < nd) {
+                    flag = P.item_done + C.deps[tid];
+                }
+                bool mine = flag == nullptr || ld_acquire(flag) >= need;
+                if (!__all_sync(FULL, mine)) {
+                    const unsigned long long t0 = global_ns();
+                    for (;;) {
+                        __nanosleep(32);
+                        if (!mine) mine = ld_acquire(flag) >= need;
+                        if (__all_sync(FULL, mine)) break;
+                        int stop = 0;
+                        if (tid == 0) {
+                            if (*(volatile int *)P.err != 0) stop = 1;
+                            else if (global_ns() - t0 > P.timeout_ns) {
+                                if (atomicCAS(P.err, 0, DEV_TIMEOUT) == 0) { P.err[1] = it.x; P.err[2] = it.y; P.err[3] = i; }
+                                stop = 1;
+                            }
+                        }
+                        if (__shfl_sync(FULL, stop, 0)) { ok = 0; break; }
+                    }
+                }
+            }
+            if (tid == 0) s_ok = ok;
+        }
+        cp_async_wait<0>();          // this thread's copies of C's input rows have landed
+        __syncthreads();             // (A) dependencies done, C's inputs visible
+        if (!s_ok) break;
+        const bool has_next = Nx.idx < nitems;
+        if (has_next) issue_structure<T>(P, Nx);
+        cp_async_commit();
+        int t2 = 0;
+        if (tid == 64 && has_next) t2 = atomicAdd(P.ticket, 1);
+        // ---- compute C
+        if (it.z >= 0) run_stage_singletons<T, V, TR>(P, C, tile_bytes ? dyn + b * (size_t)tile_bytes : nullptr, G);
+        else run_block<T, TR>(P, it.x, ~it.z);
+        __syncthreads();             // (B) every row of C written
+        if (tid == 32) {
+            // release pattern: one fence, then the (relaxed) completion marks
+            fence_acq_rel_gpu();
+            atomicAdd(P.done + (long long)it.x * P.maxL + it.y, 1);
+            st_relaxed(P.item_done + i, 1);
+        }
+        if (tid == 64) {
+            if (has_next) load_desc(P, C, t2);
+            else C.idx = nitems;
+        }
+        cp_async_wait<0>();          // this thread's copies of Nx's structure have landed
+        __syncthreads();             // (C) Nx's structure and the following descriptor visible
+        if (!has_next) break;
+        if (tile_bytes) issue_input<T, TR>(P, Nx, dyn + (b ^ 1) * (size_t)tile_bytes);
+        cp_async_commit();
+    }
+    cp_async_wait<0>();
+}
+
 // g[j][r] = sum_a cq_a[j] lam_a[j][r] in source order.  FP64 path: FP64 products and
 // sum.  FP32 path: FP32 products with a compensated (Kahan) FP32 sum, so the rounding
 // error does not grow with the number of sources (B300's FP64 rate would make an FP64
@@ -585,6 +808,75 @@ __global__ void k_source_sum(long long N, int S, int R, const T *__restrict__ cq
         }
     }
     g[j * ld_g + r] = acc;
+}
+
+// Vector form of the same sum (same operations per element, in the same source order):
+// a CTA takes a tile of rows j, stages pos_a[j] and cq_a[j] of up to SUM_STAGE sources in
+// shared memory, and each thread (one row, one V-wide column chunk) then issues the
+// row loads of SUM_GRP sources at once.  The loads of lam stream (evict-first).
+constexpr int SUM_STAGE = 32;
+constexpr int SUM_GRP = 12;
+constexpr int SUM_ROWS = 64;
+
+template <typename T, int V>
+__global__ void __launch_bounds__(256) k_source_sum_vec(long long N, int S, int R, int rows,
+                                                        const T *__restrict__ cqn, const int *__restrict__ pos,
+                                                        const T *__restrict__ lam, long long ld_lam, T *__restrict__ g,
+                                                        long long ld_g)
+{
+    using VT = typename VecT<T, V>::type;
+    __shared__ int s_pos[SUM_STAGE * SUM_ROWS];
+    __shared__ T s_c[SUM_STAGE * SUM_ROWS];
+    const int L = R / V;
+    const int t = threadIdx.x, row = t / L, c = t - row * L;
+    const long long j0 = (long long)blockIdx.x * rows, j = j0 + row;
+    const int r = c * V;
+    Pack<T, V> acc, comp;
+#pragma unroll
+    for (int u = 0; u < V; ++u) { acc.v[u] = T(0); comp.v[u] = T(0); }
+    for (int s0 = 0; s0 < S; s0 += SUM_STAGE) {
+        const int ns = min(SUM_STAGE, S - s0);
+        __syncthreads();
+        for (int q = t; q < ns * rows; q += blockDim.x) {
+            const int a = q / rows, rr = q - a * rows;
+            const long long jj = j0 + rr;
+            if (jj < N) {
+                s_pos[a * rows + rr] = __ldg(pos + (long long)(s0 + a) * N + jj);
+                s_c[a * rows + rr] = __ldg(cqn + (long long)(s0 + a) * N + jj);
+            }
+        }
+        __syncthreads();
+        if (j >= N) continue;
+        for (int a0 = 0; a0 < ns; a0 += SUM_GRP) {
+            Pack<T, V> vals[SUM_GRP];
+#pragma unroll
+            for (int b = 0; b < SUM_GRP; ++b)
+                if (a0 + b < ns) {
+                    const int a = a0 + b;
+                    const VT x = __ldcs(reinterpret_cast<const VT *>(
+                        lam + ((long long)(s0 + a) * N + s_pos[a * rows + row]) * ld_lam + r));
+                    memcpy(&vals[b], &x, sizeof(VT));
+                }
+#pragma unroll
+            for (int b = 0; b < SUM_GRP; ++b)
+                if (a0 + b < ns) {
+                    const T cc = s_c[(a0 + b) * rows + row];
+#pragma unroll
+                    for (int u = 0; u < V; ++u) {
+                        const T prod = cc * vals[b].v[u];
+                        if (sizeof(T) == 8) {
+                            acc.v[u] += prod;
+                        } else {
+                            const T y = prod - comp.v[u];
+                            const T tt = acc.v[u] + y;
+                            comp.v[u] = (tt - acc.v[u]) - y;
+                            acc.v[u] = tt;
+                        }
+                    }
+                }
+        }
+    }
+    if (j < N) store<T, V>(g + j * ld_g + r, acc);
 }
 
 // receiver sampling P: out[a][k] = field[a][rec[a][k]]
@@ -741,18 +1033,24 @@ static int launch_traverse(Tangent *t, TravParams &P, int G, cudaStream_t st)
         EIK_CHECK(cudaGraphLaunch(exec, st));
         return EIK_OK;
     }
-    // persistent: slots of G lanes, one node in flight per slot, at most 256 threads
-    const int threads = std::min(256, std::max(32, t->item_max * G));
+    // persistent: 256 threads, input rows staged in shared memory when they are whole
+    // 16-byte chunks and an item's rows fit 32 KB
+    const bool tile = V * sizeof(T) == 16 && rowb % 16 == 0 && (P.ld_in * sizeof(T)) % 16 == 0 &&
+                      ((uintptr_t)P.in & 15) == 0 && (size_t)t->item_max * rowb <= 32768;
+    const int tile_bytes = tile ? (int)(t->item_max * rowb) : 0;
+    const size_t dyn = 2 * (size_t)tile_bytes;
+    EIK_CHECK(cudaFuncSetAttribute(k_traverse_persistent<T, V, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = t->opts.ctas_per_sm;
     if (per_sm <= 0) {
-        EIK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_persistent<T, V, TR>, threads, 0));
+        EIK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_persistent<T, V, TR>, 256, dyn));
         per_sm = std::max(per_sm, 1);
     }
     long long grid = std::min<long long>((long long)t->num_sms * per_sm, P.nitems);
     grid = std::max<long long>(grid, 1);
     EIK_CHECK(cudaMemsetAsync(P.done, 0, (size_t)t->S * t->maxL * sizeof(int), st));
     EIK_CHECK(cudaMemsetAsync(P.ticket, 0, sizeof(int), st));
-    k_traverse_persistent<T, V, TR><<<(unsigned)grid, threads, 0, st>>>(P, G);
+    EIK_CHECK(cudaMemsetAsync(P.item_done, 0, (size_t)std::max(P.nitems, 1) * sizeof(int), st));
+    k_traverse_persistent<T, V, TR><<<(unsigned)grid, 256, dyn, st>>>(P, G, tile_bytes);
     EIK_CHECK_LAUNCH();
     return EIK_OK;
 }
@@ -830,20 +1128,37 @@ int traverse(Tangent *t, bool TR, int mode, const void *in, int shared_in, int R
         P.ebeg = TR ? t->ebeg_bwd : t->ebeg_fwd;
         P.item_cnt = t->item_cnt + (TR ? (size_t)t->S * t->maxL : 0);
         P.done = t->done; P.ticket = t->ticket; P.err = t->err;
+        P.deps = TR ? t->deps_bwd : t->deps_fwd;
+        // while a test hold is in place every item takes the level wait it targets
+        P.ndeps = t->opts.item_deps && t->holds.empty() ? (TR ? t->ndeps_bwd : t->ndeps_fwd) : nullptr;
+        P.item_done = t->item_done;
         P.blk_desc = t->blk_desc; P.blk_off = t->blk_off; P.binv = t->binv; P.ws = t->ws_blk;
         P.timeout_ns = (unsigned long long)(t->opts.wait_timeout_s * 1e9);
         if (dtype == EIK_F32) rc = TR ? dispatch_v<float, true>(t, P, st) : dispatch_v<float, false>(t, P, st);
         else rc = TR ? dispatch_v<double, true>(t, P, st) : dispatch_v<double, false>(t, P, st);
         if (rc) return rc;
         if (TR && mode == MODE_J && sum_sources && out_aux) {
-            long long n = t->N * w;
-            unsigned blocks = (unsigned)((n + 255) / 256);
-            if (dtype == EIK_F32)
-                k_source_sum<float><<<blocks, 256, 0, st>>>(t->N, t->S, w, t->cqn32, t->pos, (const float *)xp, P.ld_x,
-                                                            (float *)auxp, (long long)R);
-            else
-                k_source_sum<double><<<blocks, 256, 0, st>>>(t->N, t->S, w, t->cqn64, t->pos, (const double *)xp, P.ld_x,
-                                                             (double *)auxp, (long long)R);
+            const int V = dtype == EIK_F32 ? 4 : 2;
+            const int L = w / V;
+            if (w % V == 0 && R % V == 0 && r0 % V == 0 && aligned16(xp) && aligned16(auxp) && L <= 256) {
+                const int rows = std::min(SUM_ROWS, std::max(1, 256 / L));
+                const unsigned blocks = (unsigned)((t->N + rows - 1) / rows);
+                if (dtype == EIK_F32)
+                    k_source_sum_vec<float, 4><<<blocks, rows * L, 0, st>>>(t->N, t->S, w, rows, t->cqn32, t->pos,
+                                                                            (const float *)xp, P.ld_x, (float *)auxp, (long long)R);
+                else
+                    k_source_sum_vec<double, 2><<<blocks, rows * L, 0, st>>>(t->N, t->S, w, rows, t->cqn64, t->pos,
+                                                                             (const double *)xp, P.ld_x, (double *)auxp, (long long)R);
+            } else {
+                long long n = t->N * w;
+                unsigned blocks = (unsigned)((n + 255) / 256);
+                if (dtype == EIK_F32)
+                    k_source_sum<float><<<blocks, 256, 0, st>>>(t->N, t->S, w, t->cqn32, t->pos, (const float *)xp, P.ld_x,
+                                                                (float *)auxp, (long long)R);
+                else
+                    k_source_sum<double><<<blocks, 256, 0, st>>>(t->N, t->S, w, t->cqn64, t->pos, (const double *)xp, P.ld_x,
+                                                                 (double *)auxp, (long long)R);
+            }
             EIK_CHECK_LAUNCH();
         }
     }

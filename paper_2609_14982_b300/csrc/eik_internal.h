@@ -28,6 +28,9 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
 // eik_opts.chunk picks the item size actually used (default: the capacity).
 constexpr int ITEM_MAX = 64;
 
+// Most dependencies recorded per work item.
+constexpr int DEP_MAX = 32;
+
 // Device-side fault codes latched in Tangent::err (first one wins).
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_SINGULAR = 2, DEV_BAD_INDEX = 3 };
 
@@ -113,6 +116,11 @@ struct Tangent {
     int2 *ebeg_bwd = nullptr;
     std::vector<int> step_ptr_fwd, step_ptr_bwd;   // [maxL+1] items per step (host)
     int *item_cnt = nullptr;      // [S][maxL] items per (source, level); bwd uses reversed step
+    // per-item dependencies: the items holding the upstream positions of an item's rows
+    // (at most DEP_MAX, else the item waits for its whole previous step), per direction
+    int *deps_fwd = nullptr, *deps_bwd = nullptr;     // [nitems][DEP_MAX]
+    int *ndeps_fwd = nullptr, *ndeps_bwd = nullptr;   // [nitems], -1 = overflow
+    int *item_done = nullptr;     // [nitems] 1 once the item of the current traversal finished
     int *done = nullptr;          // [S][maxL] completed items per (source, step)
     int *ticket = nullptr;        // [2]
     int *err = nullptr;           // [4] device fault latch {code, source, step, item}

@@ -716,6 +716,58 @@ __global__ void k_block_inverse(const int4 *__restrict__ desc, const long long *
     }
 }
 
+// Item index of every canonical position, one direction's item list.  A singleton
+// item's range also spans the members of the level's nontrivial blocks (perm < 0),
+// which belong to their block items instead.
+__global__ void k_item_of_pos(int n, long long N, const int4 *__restrict__ items, const int4 *__restrict__ blk_desc,
+                              const int *__restrict__ perm, int *iop)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int4 it = items[i];
+    const bool blk = it.z < 0;
+    int p0, p1;
+    if (!blk) { p0 = it.z; p1 = it.w; }
+    else { int4 d = blk_desc[~it.z]; p0 = d.y; p1 = d.y + d.z; }
+    const long long o = (long long)it.x * N;
+    for (int p = p0; p < p1; ++p)
+        if (blk || perm[o + p] >= 0) iop[o + p] = i;
+}
+
+// The distinct items holding the upstream positions of the rows item i computes (all
+// at lower steps, hence lower tickets); -1 when there are more than DEP_MAX.
+__global__ void k_item_deps(int n, long long N, const int4 *__restrict__ items, const int4 *__restrict__ blk_desc,
+                            const int *__restrict__ perm, const int *__restrict__ rowptr, const int *__restrict__ enode,
+                            const long long *__restrict__ ebase, const int *__restrict__ iop, int *deps, int *ndeps)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int4 it = items[i];
+    const bool blk = it.z < 0;
+    int p0, p1;
+    if (!blk) { p0 = it.z; p1 = it.w; }
+    else { int4 d = blk_desc[~it.z]; p0 = d.y; p1 = d.y + d.z; }
+    const long long o = (long long)it.x * N;
+    const int *rp = rowptr + (long long)it.x * (N + 1);
+    const int *en = enode + ebase[it.x];
+    const int *io = iop + o;
+    int m = 0;
+    int *out = deps + (long long)i * DEP_MAX;
+    for (int p = p0; p < p1 && m >= 0; ++p) {
+        if (!blk && perm[o + p] < 0) continue;
+        for (int e = rp[p]; e < rp[p + 1]; ++e) {
+            int d = io[en[e]];
+            if (d == i) continue;
+            bool seen = false;
+            for (int q = 0; q < m; ++q) if (out[q] == d) { seen = true; break; }
+            if (seen) continue;
+            if (m == DEP_MAX) { m = -1; break; }
+            out[m++] = d;
+        }
+    }
+    ndeps[i] = m;
+}
+
 __global__ void k_compact_heads(long long SN, const int *head, const int *scan, int *hpos)
 {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -763,7 +815,8 @@ void free_tangent(Tangent *t)
     void *ptrs[] = {t->perm, t->pos, t->label, t->level, t->rowptr, t->up_node, t->up_w32, t->up_w64, t->cptr,
                     t->dn_node, t->dn_w32, t->dn_w64, t->cq64, t->cq32, t->cqn64, t->cqn32, t->rec_slot,
                     t->rec_nat, t->nrow_cnt, t->nrow_node, t->nrow_w, t->cs_nat, t->blk_desc, t->blk_off, t->lu,
-                    t->binv, t->piv, t->items_fwd, t->items_bwd, t->ebeg_fwd, t->ebeg_bwd, t->item_cnt, t->done, t->ticket, t->err, t->ws_vec,
+                    t->binv, t->piv, t->items_fwd, t->items_bwd, t->ebeg_fwd, t->ebeg_bwd, t->deps_fwd, t->deps_bwd,
+                    t->ndeps_fwd, t->ndeps_bwd, t->item_done, t->item_cnt, t->done, t->ticket, t->err, t->ws_vec,
                     t->ws_blk, t->ebase_d, t->tbase_d};
     for (void *p : ptrs) if (p) cudaFree(p);
     if (t->params_d) cudaFree((void *)t->params_d);
@@ -1153,6 +1206,22 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
         TRY(dalloc(&t->ebeg_bwd, bw.size()));
         k_item_edges<<<blocks_for((long long)fw.size()), 256, 0, st>>>((int)fw.size(), N, t->items_fwd, t->rowptr, t->ebeg_fwd);
         k_item_edges<<<blocks_for((long long)bw.size()), 256, 0, st>>>((int)bw.size(), N, t->items_bwd, t->cptr, t->ebeg_bwd);
+        TRY(cudaGetLastError());
+        // per-item dependencies of both directions
+        int *iop;
+        TRY(sc.get(&iop, SN));
+        const int ni = (int)fw.size();
+        TRY(dalloc(&t->deps_fwd, (size_t)ni * DEP_MAX));
+        TRY(dalloc(&t->deps_bwd, (size_t)ni * DEP_MAX));
+        TRY(dalloc(&t->ndeps_fwd, ni));
+        TRY(dalloc(&t->ndeps_bwd, ni));
+        TRY(dalloc(&t->item_done, ni));
+        k_item_of_pos<<<blocks_for(ni), 256, 0, st>>>(ni, N, t->items_fwd, t->blk_desc, t->perm, iop);
+        k_item_deps<<<blocks_for(ni), 256, 0, st>>>(ni, N, t->items_fwd, t->blk_desc, t->perm, t->rowptr, t->up_node,
+                                                    t->ebase_d, iop, t->deps_fwd, t->ndeps_fwd);
+        k_item_of_pos<<<blocks_for(ni), 256, 0, st>>>(ni, N, t->items_bwd, t->blk_desc, t->perm, iop);
+        k_item_deps<<<blocks_for(ni), 256, 0, st>>>(ni, N, t->items_bwd, t->blk_desc, t->perm, t->cptr, t->dn_node,
+                                                    t->tbase_d, iop, t->deps_bwd, t->ndeps_bwd);
         TRY(cudaGetLastError());
     }
 

@@ -43,7 +43,7 @@ class Opts(C.Structure):
                 ("chunk", C.c_int), ("ctas_per_sm", C.c_int), ("wait_timeout_s", C.c_double),
                 ("eik_tol", C.c_double), ("eik_max_cycles", C.c_int), ("eik_src_radius", C.c_double),
                 ("sweep_tol", C.c_double), ("sweep_max_cycles", C.c_int), ("rhs_chunk", C.c_int),
-                ("eik_fp32", C.c_int), ("eik_fp64_radius", C.c_double)]
+                ("eik_fp32", C.c_int), ("eik_fp64_radius", C.c_double), ("item_deps", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -256,9 +256,9 @@ class Tangent:
         return out, cyc.value
 
     def tune(self, **kw):
-        """Change run-time options (schedule, ctas_per_sm, rhs_chunk, wait_timeout_s)."""
+        """Change run-time options (schedule, ctas_per_sm, rhs_chunk, wait_timeout_s, item_deps)."""
         for k, v in kw.items():
-            if k not in ("schedule", "ctas_per_sm", "rhs_chunk", "wait_timeout_s"):
+            if k not in ("schedule", "ctas_per_sm", "rhs_chunk", "wait_timeout_s", "item_deps"):
                 raise KeyError(k)
             setattr(self.opts, k, v)
         _check(lib().tangent_tune(self.h, C.byref(self.opts)))

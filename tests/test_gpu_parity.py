@@ -149,6 +149,23 @@ def test_levels_schedule_matches_persistent(built, dtype, sched, R):
     tan_l.status()
 
 
+@pytest.mark.parametrize("case,chunk", [("table3-41x41x25", 8), ("table3-41x41x25", 64), ("cyclic-13x13x9", 4)])
+def test_item_waits_match_level_waits(built, case, chunk):
+    """Persistent items that wait only for the items holding their upstream rows give
+    bit-identical results to items that wait for their whole previous level (same
+    kernel, same arithmetic), over repeated calls and CTA counts."""
+    g, Ts, s, srcs, otans, tan = built(case, opts=eik.default_opts(chunk=chunk))
+    q = torch.randn((len(srcs), g.N, 8), device=DEV, dtype=torch.float32, generator=torch.Generator(DEV).manual_seed(9))
+    tan.tune(item_deps=0)
+    ref = [tan.solve(q).clone(), tan.solve_T(q).clone()]
+    for per_sm in (0, 1):
+        tan.tune(item_deps=1, ctas_per_sm=per_sm)
+        for _ in range(3):
+            assert torch.equal(tan.solve(q), ref[0])
+            assert torch.equal(tan.solve_T(q), ref[1])
+    tan.status()
+
+
 @pytest.mark.parametrize("schedule", [eik.SCHED_PERSISTENT, eik.SCHED_LEVELS, eik.SCHED_STAGED])
 def test_rhs_chunking_and_tune(built, schedule):
     """Right-hand sides processed in column chunks (and options changed on a built
@@ -299,10 +316,11 @@ def test_eik_forward_homogeneous_exact():
 
 
 # --------------------------------------------------------------------------- failure paths
-def test_wait_timeout_reported_and_context_survives(built):
+@pytest.mark.parametrize("chunk", [64, 8])
+def test_wait_timeout_reported_and_context_survives(built, chunk):
     """A bounded device wait that can never be satisfied ends with EIK_ERR_TIMEOUT; the
     next traversal on the same context is correct again."""
-    opts = eik.default_opts(wait_timeout_s=0.25)
+    opts = eik.default_opts(wait_timeout_s=0.25, chunk=chunk)
     g, Ts, s, srcs, otans, tan = built("table3-21x21x13", opts=opts)
     q = torch.randn((len(srcs), g.N, 2), device=DEV, dtype=torch.float64)
     good = tan.solve(q).clone()
@@ -335,13 +353,15 @@ def test_autotuner_applies_a_setting_and_keeps_results(built, tmp_path):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_staged_schedule_jacobian_against_oracle(oracle_mod, dtype):
-    """J p and J^T y with the staged (bulk-copy) schedule against the oracle, R = 64."""
+@pytest.mark.parametrize("sched,chunk", [(eik.SCHED_STAGED, 16), (eik.SCHED_PERSISTENT, 64), (eik.SCHED_PERSISTENT, 16)])
+def test_staged_schedule_jacobian_against_oracle(oracle_mod, dtype, sched, chunk):
+    """J p and J^T y with the staged (bulk-copy) schedule and the persistent schedule
+    (shared-memory input rows at R = 64) against the oracle."""
     g, Ts, s, srcs, rec = _config1_case()
     _, G, _ = oracle_mod.metric(g)
     otans = [oracle_mod.build_tangent(g, G, Ts[a], s, int(srcs[a])) for a in range(len(srcs))]
     tan = eik.Tangent(eik.DeviceGrid(g), torch.tensor(Ts, device=DEV), torch.tensor(s, device=DEV), srcs,
-                      rec=rec, opts=eik.default_opts(schedule=eik.SCHED_STAGED, chunk=16))
+                      rec=rec, opts=eik.default_opts(schedule=sched, chunk=chunk))
     rng = np.random.default_rng(12)
     p = torch.tensor(rng.standard_normal((g.N, 64)), device=DEV, dtype=dtype)
     y = torch.tensor(rng.standard_normal((len(srcs), len(rec), 64)), device=DEV, dtype=dtype)

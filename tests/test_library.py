@@ -58,3 +58,27 @@ def test_binding_rejects_host_tensors():
     from paper_2609_14982_b300 import eik
     with pytest.raises(TypeError):
         eik._dev(torch.zeros(4), name="x")
+
+
+def test_binding_structs_match_header_layout(tmp_path):
+    """The ctypes mirrors of eik_grid, eik_opts and eik_stats have the header's field
+    offsets and sizes (compiled with the host C compiler)."""
+    import subprocess
+    from paper_2609_14982_b300 import eik
+    structs = {"eik_grid": eik.Grid_, "eik_opts": eik.Opts, "eik_stats": eik.Stats}
+    lines = ['#include <stdio.h>', '#include "eik.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {(a, b): int(c) for a, b, c in (ln.split() for ln in out if ln)}
+    for cname, py in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
