@@ -168,6 +168,8 @@ def run_ours(args):
     t_state = time.time() - t0
     sched = {"persistent": eik.SCHED_PERSISTENT, "levels": eik.SCHED_LEVELS, "staged": eik.SCHED_STAGED}[args.schedule]
     opts = eik.default_opts(schedule=sched, item_deps=0 if args.level_waits else 1, ctas_per_sm=args.ctas_per_sm)
+    if args.chunk:
+        opts.chunk = args.chunk
     t0 = time.time()
     tan = eik.Tangent(dg, T, s, src, rec=wl.rec, opts=opts)
     torch.cuda.synchronize()
@@ -463,6 +465,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--schedule", choices=["persistent", "levels", "staged"], default="persistent")
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--chunk", type=int, default=0, help="positions per work item (default: the library's, 64)")
     ap.add_argument("--level-waits", action="store_true",
                     help="persistent items wait for their whole previous level, not only their upstream items")
     ap.add_argument("--no-sweep", action="store_true")
