@@ -15,6 +15,8 @@ What it computes (paper sections in brackets):
     library direct solve (numpy dense / SciPy sparse LU)              [Eq. transport-system]
   * J = P A^-1 C M and J^T = M^T C^T A^-T P^T, summed over sources     [Sec. 4.4]
   * directional sweeping (Gauss-Seidel over 2^D orderings)            [Sec. 3.6]
+  * the augmented Gauss-Newton operator K, K^T (W_d, roughness R,
+    relative damping S_k) and LSMR on it                               [Sec. 4.5]
 
 Where the paper leaves a detail open the oracle takes one stated reading (face
 averages, boundary stencils, canonical order); those readings are pinned by the
@@ -389,3 +391,120 @@ def lsqr(apply_J, apply_JT, b: np.ndarray, iters: int):
         x = x + (phi / rho) * w
         w = v - (theta / rho) * w
     return x, phibar
+
+
+# --------------------------------------------------------------------------- Sec. 4.5
+def roughness(grid):
+    """R, the model-increment roughness operator of Eq. (gn-subproblem).  The paper does
+    not define it; reading: first differences along every logical axis, unit weight,
+    (R p)_row = p[i + e_d] - p[i] for every node pair adjacent along axis d.  Rows are
+    ordered axis by axis, and within an axis by the linear index of the lower node.
+    Returns a scipy.sparse CSR matrix [n_rough, N]."""
+    import scipy.sparse as sp
+    n = tuple(int(x) for x in grid.n[:grid.ndim])
+    N = int(np.prod(n))
+    idx = np.arange(N).reshape(n)
+    rows, cols, vals = [], [], []
+    r0 = 0
+    for d in range(len(n)):
+        lo = np.take(idx, np.arange(n[d] - 1), axis=d).ravel()
+        hi = np.take(idx, np.arange(1, n[d]), axis=d).ravel()
+        order = np.argsort(lo, kind="stable")
+        lo, hi = lo[order], hi[order]
+        m = len(lo)
+        r = r0 + np.arange(m)
+        rows += [r, r]
+        cols += [hi, lo]
+        vals += [np.ones(m), -np.ones(m)]
+        r0 += m
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(r0, N))
+
+
+def gn_operator(grid, tans, s, rec, wd, vk, lam, gamma, model=MODEL_VELOCITY):
+    """The augmented Gauss-Newton operator of Eq. (augmented-actions):
+        K p   = [W_d J p ; lam R p ; lam S p],        S = gamma diag(1 / v_k)  (Eq. relative-damping)
+        K^T y = J^T W_d y_d + lam R^T y_R + lam S^T y_S.
+    wd: [S, n_rec] diagonal of W_d; vk: [N] current model.  p is [N]; y is
+    [S*n_rec + n_rough + N].  Returns (apply_K, apply_KT, n_rows)."""
+    Rm = roughness(grid)
+    S_, nr = len(tans), len(rec)
+    nd, nR, N = S_ * nr, Rm.shape[0], len(vk)
+    sdiag = gamma / np.asarray(vk, dtype=np.float64)
+
+    def apply_K(p):
+        d = J(tans, s, rec, p[:, None], model=model)[:, :, 0] * wd
+        return np.concatenate([d.ravel(), lam * (Rm @ p), lam * sdiag * p])
+
+    def apply_KT(y):
+        yd = (y[:nd].reshape(S_, nr) * wd)[:, :, None]
+        g = JT(tans, s, rec, yd, model=model)[:, 0]
+        return g + lam * (Rm.T @ y[nd:nd + nR]) + lam * sdiag * y[nd + nR:]
+
+    return apply_K, apply_KT, nd + nR + N
+
+
+def lsmr(apply_A, apply_AT, b: np.ndarray, iters: int):
+    """LSMR (Fong and Saunders, 2011), plain numpy, x0 = 0, no damping: the Krylov solver
+    that Sec. 4.5 applies to the augmented system.  Golub-Kahan bidiagonalization, the
+    first QR (rotations P_k) of B_k, the second QR (rotations Pbar_k) of [R_k^T; theta e_k^T],
+    and x updated through the h, hbar recurrences.  The residual norm |b - A x_k| is
+    carried by a third rotation sequence (Ptilde) applied to R_bar^T and to the rotated
+    right-hand side; |A^T r_k| = |zetabar_{k+1}|.
+    Returns (x, info) with info = {normr, normar, norma, normx, iters}."""
+    beta = np.linalg.norm(b)
+    u = b / beta
+    v = apply_AT(u)
+    alpha = np.linalg.norm(v)
+    v = v / alpha
+    x = np.zeros_like(v)
+    h = v.copy()
+    hbar = np.zeros_like(v)
+    alphabar, zetabar = alpha, alpha * beta
+    rho, rhobar, cbar, sbar, zeta = 1.0, 1.0, 1.0, 0.0, 0.0
+    # residual-norm recurrences
+    betadd, betad, rhodot, thetatilde, tautilde_prev, done2 = beta, 0.0, 1.0, 0.0, 0.0, 0.0
+    norma2 = alpha * alpha
+    normr = beta
+    for _ in range(iters):
+        u = apply_A(v) - alpha * u
+        beta = np.linalg.norm(u)
+        u = u / beta
+        v = apply_AT(u) - beta * v
+        alpha = np.linalg.norm(v)
+        v = v / alpha
+        norma2 += beta * beta + alpha * alpha
+        # P_k: eliminate beta_{k+1} from B_k
+        rho_prev = rho
+        rho = np.hypot(alphabar, beta)
+        c, s = alphabar / rho, beta / rho
+        theta = s * alpha
+        alphabar = c * alpha
+        # Pbar_k: eliminate theta_{k+1} from [R_k^T; theta e_k^T]
+        rhobar_prev, zeta_prev = rhobar, zeta
+        thetabar = sbar * rho
+        rhobar = np.hypot(cbar * rho, theta)
+        cbar, sbar = cbar * rho / rhobar, theta / rhobar
+        zeta = cbar * zetabar
+        zetabar = -sbar * zetabar
+        # h, hbar, x
+        hbar = h - (thetabar * rho / (rho_prev * rhobar_prev)) * hbar
+        x = x + (zeta / (rho * rhobar)) * hbar
+        h = v - (theta / rho) * h
+        # |r_k|: P_k on the right-hand side, then Ptilde_{k-1} on Rbar^T and on it
+        betahat = c * betadd
+        betadd = -s * betadd
+        rhotilde = np.hypot(rhodot, thetabar)
+        ctilde, stilde = rhodot / rhotilde, thetabar / rhotilde
+        thetatilde_prev = thetatilde
+        thetatilde = stilde * rhobar
+        rhodot = ctilde * rhobar
+        betatilde = ctilde * betad + stilde * betahat
+        betad = -stilde * betad + ctilde * betahat
+        tautilde = (zeta_prev - thetatilde_prev * tautilde_prev) / rhotilde
+        taudot = (zeta - thetatilde * tautilde) / rhodot
+        done2 += (betatilde - tautilde) ** 2
+        tautilde_prev = tautilde
+        normr = np.sqrt(done2 + (betad - taudot) ** 2 + betadd ** 2)
+    info = {"normr": float(normr), "normar": float(abs(zetabar)), "norma": float(np.sqrt(norma2)),
+            "normx": float(np.linalg.norm(x)), "iters": iters}
+    return x, info
