@@ -312,6 +312,48 @@ int lsqr_iterate(eik_lsqr *l, int iters, int use_graph, eik_stream stream);
 int lsqr_solution(eik_lsqr *l, void *x, double *scalars, eik_stream stream);
 void lsqr_free(eik_lsqr *l);
 
+/*
+ * The augmented Gauss-Newton operator of Sec. 4.5 (Eq. augmented-ls, Eq.
+ * augmented-actions) on a built tangent, one model vector:
+ *   K p   = [ W_d J p ; lambda R p ; lambda S p ]              S = gamma diag(1 / v_k)
+ *   K^T y = J^T W_d y_d + lambda R^T y_R + lambda S^T y_S      (Eq. relative-damping)
+ * J is the tangent's Jacobian with its model map (the paper's model is the nodal
+ * velocity: build the tangent with EIK_MODEL_VELOCITY).  R, which the paper leaves
+ * undefined, is read as unit first differences along every logical axis:
+ * (R p)_row = p[i + e_d] - p[i], rows axis by axis, within an axis in the linear order of
+ * the lower node i; n_rough = sum over d of (n_d - 1) x prod of the other extents.
+ * K-space vectors are [n_data + n_rough + N]: the data block [S][n_rec], then R's rows,
+ * then the N damping rows.  Vectors are FP64 or FP32 per dtype; W_d, S and all scalars
+ * are FP64.
+ *   gn_create     wd: device FP64 [S][n_rec], the diagonal of W_d; vk: device FP64 [N],
+ *                 the current model (positive).  Both are copied; the caller keeps them.
+ *                 lambda >= 0, gamma >= 0.  The solver owns its work vectors; the tangent
+ *                 must outlive it.  Synchronizes the device once.
+ *   gn_dims       host outputs (each may be NULL): rows of K, data rows, roughness rows
+ *   gn_apply      p device [N] -> out device [n_rows]  (K p)
+ *   gn_apply_T    y device [n_rows] -> out device [N]  (K^T y)
+ * LSMR (Fong & Saunders 2011; x0 = 0, no extra damping: the regularization is in K) on
+ * min |K x - b|, with every vector and scalar on the device:
+ *   gn_lsmr_start    b device [n_rows] (e.g. [-W_d r_k; 0; 0]): beta u = b, alpha v = K^T u
+ *   gn_lsmr_iterate  runs `iters` iterations; use_graph != 0 captures one iteration into
+ *                    a CUDA graph on the first call (not on the legacy default stream)
+ *   gn_lsmr_solution copies x (device [N], may be NULL) and, if scalars != NULL, the host
+ *                    doubles {|r_k| (recurrence), |K^T r_k|, |K| estimate (Frobenius of
+ *                    the bidiagonal), |x_k|, |b|, iterations}; a caller stops when
+ *                    |K^T r| <= atol |K| |r| (the paper uses 1e-4)
+ *   gn_free          releases the solver (not the tangent)
+ */
+typedef struct eik_gn eik_gn;
+int gn_create(eik_tangent *t, const double *wd, const double *vk, double lambda, double gamma, int dtype,
+              eik_gn **out);
+int gn_dims(const eik_gn *g, int64_t *n_rows, int64_t *n_data, int64_t *n_rough);
+int gn_apply(eik_gn *g, const void *p, void *out, eik_stream stream);
+int gn_apply_T(eik_gn *g, const void *y, void *out, eik_stream stream);
+int gn_lsmr_start(eik_gn *g, const void *b, eik_stream stream);
+int gn_lsmr_iterate(eik_gn *g, int iters, int use_graph, eik_stream stream);
+int gn_lsmr_solution(eik_gn *g, void *x, double *scalars, eik_stream stream);
+void gn_free(eik_gn *g);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,9 @@ EXPORTED = ["eik_opts_default", "eik_last_error", "eik_version", "eik_forward", 
             "tangent_apply_T", "tangent_solve", "tangent_solve_T", "tangent_sample", "tangent_stats", "tangent_dims",
             "tangent_export", "tangent_status", "tangent_free", "sweep_apply", "tangent_debug_hold", "tangent_tune",
             "lsqr_create", "lsqr_start", "lsqr_iterate", "lsqr_solution", "lsqr_free",
-            "eik_forward_noalloc", "eik_forward_noalloc_capacity"]
+            "eik_forward_noalloc", "eik_forward_noalloc_capacity",
+            "gn_create", "gn_dims", "gn_apply", "gn_apply_T", "gn_lsmr_start", "gn_lsmr_iterate",
+            "gn_lsmr_solution", "gn_free"]
 
 
 class EikError(RuntimeError):
@@ -91,6 +93,15 @@ def lib():
         L.lsqr_solution.argtypes = [P, P, P, P]
         L.lsqr_free.argtypes = [P]
         L.lsqr_free.restype = None
+        L.gn_create.argtypes = [P, P, P, D, D, I, C.POINTER(P)]
+        L.gn_dims.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.gn_apply.argtypes = [P, P, P, P]
+        L.gn_apply_T.argtypes = [P, P, P, P]
+        L.gn_lsmr_start.argtypes = [P, P, P]
+        L.gn_lsmr_iterate.argtypes = [P, I, I, P]
+        L.gn_lsmr_solution.argtypes = [P, P, P, P]
+        L.gn_free.argtypes = [P]
+        L.gn_free.restype = None
         L.sweep_apply.argtypes = [P, I, P, I, P, I, C.POINTER(Opts), C.POINTER(I), P]
         _lib = L
     return _lib
@@ -324,3 +335,73 @@ class LSQR:
         _check(lib().lsqr_solution(self.h, _dev(x, self.dtype, "x"), sc, _stream()))
         names = ("alpha", "beta", "rhobar", "phibar", "phi", "rho", "theta", "c", "s")
         return x, dict(zip(names, list(sc)))
+
+
+class GN:
+    """The augmented Gauss-Newton operator K = [W_d J; lam R; lam S_k] of a tangent and
+    device LSMR on it (one model vector).  wd: [S, n_rec] FP64 data weights (diagonal of
+    W_d); vk: [N] FP64 current model (S_k = gamma diag(1 / vk))."""
+
+    def __init__(self, tan: Tangent, wd: torch.Tensor, vk: torch.Tensor, lam: float, gamma: float,
+                 dtype=torch.float64):
+        self.tan = tan
+        self.dtype = dtype
+        h = C.c_void_p()
+        _check(lib().gn_create(tan.h, _dev(wd, torch.float64, "wd"), _dev(vk, torch.float64, "vk"), float(lam),
+                               float(gamma), _dt(dtype), C.byref(h)))
+        self.h = h
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib().gn_dims(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        self.n_rows, self.n_data, self.n_rough = a.value, b.value, c.value
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().gn_free(self.h)
+            self.h = C.c_void_p()
+
+    def apply(self, p: torch.Tensor) -> torch.Tensor:
+        out = torch.empty(self.n_rows, dtype=self.dtype, device="cuda")
+        _check(lib().gn_apply(self.h, _dev(p, self.dtype, "p"), _dev(out, self.dtype, "out"), _stream()))
+        return out
+
+    def apply_T(self, y: torch.Tensor) -> torch.Tensor:
+        out = torch.empty(self.tan.N, dtype=self.dtype, device="cuda")
+        _check(lib().gn_apply_T(self.h, _dev(y, self.dtype, "y"), _dev(out, self.dtype, "out"), _stream()))
+        return out
+
+    def rhs(self, r: torch.Tensor, wd: torch.Tensor) -> torch.Tensor:
+        """b = [-W_d r; 0; 0] of Eq. (augmented-ls) for a residual r [S, n_rec]."""
+        b = torch.zeros(self.n_rows, dtype=self.dtype, device="cuda")
+        b[:self.n_data] = (-(wd * r)).reshape(-1).to(self.dtype)
+        return b
+
+    def start(self, b: torch.Tensor):
+        _check(lib().gn_lsmr_start(self.h, _dev(b, self.dtype, "b"), _stream()))
+
+    def iterate(self, iters: int, use_graph: bool = True):
+        _check(lib().gn_lsmr_iterate(self.h, iters, int(use_graph), _stream()))
+
+    def solution(self):
+        x = torch.empty(self.tan.N, dtype=self.dtype, device="cuda")
+        sc = (C.c_double * 6)()
+        _check(lib().gn_lsmr_solution(self.h, _dev(x, self.dtype, "x"), sc, _stream()))
+        names = ("normr", "normar", "norma", "normx", "normb", "iters")
+        return x, dict(zip(names, list(sc)))
+
+    def lsmr(self, b: torch.Tensor, atol: float = 1e-4, max_iters: int = 200, check_every: int = 5,
+             use_graph: bool = True):
+        """LSMR until |K^T r| <= atol |K| |r| (checked every `check_every` iterations) or
+        max_iters; returns (x, scalars)."""
+        self.start(b)
+        done = 0
+        while done < max_iters:
+            k = min(check_every, max_iters - done)
+            self.iterate(k, use_graph)
+            done += k
+            x, sc = self.solution()
+            if sc["normar"] <= atol * sc["norma"] * sc["normr"]:
+                break
+        return x, sc
