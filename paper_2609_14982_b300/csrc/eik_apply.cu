@@ -749,7 +749,7 @@ __global__ void __launch_bounds__(256, 4) k_traverse_persistent(TravParams P, in
         if (has_next) issue_structure<T>(P, Nx);
         cp_async_commit();
         int t2 = 0;
-        if (tid == 64 && has_next) t2 = atomicAdd(P.ticket, 1);
+        if (tid == 1 && has_next) t2 = atomicAdd(P.ticket, 1);   // its value is first needed after (B)
         // ---- compute C
         if (it.z >= 0) run_stage_singletons<T, V, TR>(P, C, tile_bytes ? dyn + b * (size_t)tile_bytes : nullptr, G);
         else run_block<T, TR>(P, it.x, ~it.z);
@@ -760,7 +760,7 @@ __global__ void __launch_bounds__(256, 4) k_traverse_persistent(TravParams P, in
             atomicAdd(P.done + (long long)it.x * P.maxL + it.y, 1);
             st_relaxed(P.item_done + i, 1);
         }
-        if (tid == 64) {
+        if (tid == 1) {
             if (has_next) load_desc(P, C, t2);
             else C.idx = nitems;
         }
@@ -1033,8 +1033,10 @@ static int launch_traverse(Tangent *t, TravParams &P, int G, cudaStream_t st)
         EIK_CHECK(cudaGraphLaunch(exec, st));
         return EIK_OK;
     }
-    // persistent: 256 threads, input rows staged in shared memory when they are whole
-    // 16-byte chunks and an item's rows fit 32 KB
+    // persistent: one thread per (position, lane) of an item, between 64 (two warps: the
+    // waiting warp and the releasing thread 32) and 256; input rows staged in shared
+    // memory when they are whole 16-byte chunks and an item's rows fit 32 KB
+    const int threads = std::min(256, std::max(64, (t->item_max * G + 31) / 32 * 32));
     const bool tile = V * sizeof(T) == 16 && rowb % 16 == 0 && (P.ld_in * sizeof(T)) % 16 == 0 &&
                       ((uintptr_t)P.in & 15) == 0 && (size_t)t->item_max * rowb <= 32768;
     const int tile_bytes = tile ? (int)(t->item_max * rowb) : 0;
@@ -1042,7 +1044,7 @@ static int launch_traverse(Tangent *t, TravParams &P, int G, cudaStream_t st)
     EIK_CHECK(cudaFuncSetAttribute(k_traverse_persistent<T, V, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = t->opts.ctas_per_sm;
     if (per_sm <= 0) {
-        EIK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_persistent<T, V, TR>, 256, dyn));
+        EIK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_persistent<T, V, TR>, threads, dyn));
         per_sm = std::max(per_sm, 1);
     }
     long long grid = std::min<long long>((long long)t->num_sms * per_sm, P.nitems);
@@ -1050,7 +1052,7 @@ static int launch_traverse(Tangent *t, TravParams &P, int G, cudaStream_t st)
     EIK_CHECK(cudaMemsetAsync(P.done, 0, (size_t)t->S * t->maxL * sizeof(int), st));
     EIK_CHECK(cudaMemsetAsync(P.ticket, 0, sizeof(int), st));
     EIK_CHECK(cudaMemsetAsync(P.item_done, 0, (size_t)std::max(P.nitems, 1) * sizeof(int), st));
-    k_traverse_persistent<T, V, TR><<<(unsigned)grid, 256, dyn, st>>>(P, G, tile_bytes);
+    k_traverse_persistent<T, V, TR><<<(unsigned)grid, threads, dyn, st>>>(P, G, tile_bytes);
     EIK_CHECK_LAUNCH();
     return EIK_OK;
 }
