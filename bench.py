@@ -455,6 +455,75 @@ def run_gn(args):
     tan.free()
 
 
+def run_stress(args):
+    """Config 5, the uneven-batch stress case: three steep-hill grids (slopes up to about
+    55 deg), 101x101x51 (32 sources, R = 8), 161x121x61 (32, R = 32) and 201x201x101 (64,
+    R = 128; a [S][N][R] FP32 field is 134 GB there, so the right-hand sides go through the
+    traversal in chunks of 32).  Per grid: state (FP32 far field), build, then J p + J^T y
+    pairs timed with CUDA events.  value = all grids' node-updates / all grids' time."""
+    import torch
+
+    from paper_2609_14982_b300 import eik
+    from paper_2609_14982_b300 import workloads as W
+    torch.cuda.set_device(0)
+    grids, tot_upd, tot_ms = [], 0.0, 0.0
+    for w in range(3):
+        wl = W.config5_grid(w)
+        g = wl.grid
+        S, N, R = wl.S, g.N, wl.R
+        dg = eik.DeviceGrid(g)
+        s = torch.tensor(wl.s, device="cuda")
+        t0 = time.time()
+        T, cyc = eik.eik_forward(dg, s, wl.src, opts=eik.default_opts(eik_fp32=1))
+        torch.cuda.synchronize()
+        t_state = time.time() - t0
+        chunk = 32 if R > 32 else 0
+        t0 = time.time()
+        tan = eik.Tangent(dg, T, s, wl.src, rec=wl.rec, opts=eik.default_opts(rhs_chunk=chunk))
+        torch.cuda.synchronize()
+        t_build = time.time() - t0
+        del T
+        st = [tan.stats(a) for a in range(S)]
+        gen = torch.Generator("cuda").manual_seed(wl.seed)
+        p = torch.randn((N, R), device="cuda", generator=gen)
+        y = torch.randn((S, len(wl.rec), R), device="cuda", generator=gen)
+        for _ in range(max(args.warmup, 1)):
+            tan.apply(p, shared_model=True)
+            tan.apply_T(y, sum_sources=True)
+        steps = max(args.steps // 2, 3)
+        tf, tb = [], []
+        for _ in range(steps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            tan.apply(p, shared_model=True)
+            e[1].record()
+            tan.apply_T(y, sum_sources=True)
+            e[2].record()
+            torch.cuda.synchronize()
+            tf.append(e[0].elapsed_time(e[1]))
+            tb.append(e[1].elapsed_time(e[2]))
+        tan.status()
+        ms = statistics.median(tf) + statistics.median(tb)
+        upd = 2.0 * N * S * R
+        tot_upd += upd * steps
+        tot_ms += sum(tf) + sum(tb)
+        grids.append({"grid": list(g.n), "nodes": N, "sources": S, "rhs": R, "receivers": len(wl.rec),
+                      "rhs_chunk": chunk, "max_slope_deg": round(wl.notes.get("max_slope_deg", 0.0), 1),
+                      "ms_fwd": round(statistics.median(tf), 3), "ms_bwd": round(statistics.median(tb), 3),
+                      "node_updates_per_s": upd / (ms / 1e3), "levels_max": max(x["levels"] for x in st),
+                      "nontrivial_scc": sum(x["nontrivial"] for x in st), "largest_scc": max(x["largest"] for x in st),
+                      "eik_forward_s": round(t_state, 2), "eik_cycles": cyc, "tangent_build_s": round(t_build, 2)})
+        del p, y
+        tan.free()
+        torch.cuda.empty_cache()
+    out = {"metric": METRIC, "value": tot_upd / (tot_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+           "warmup": max(args.warmup, 1), "ms_per_step": tot_ms / steps, "higher_is_better": True,
+           "dtype": "f32+f64blocks", "data": "synthetic (seeded steep-hill recipe; no public dataset)",
+           "config": {"workload": "3d-stress: 101x101x51 S32 R8 + 161x121x61 S32 R32 + 201x201x101 S64 R128",
+                      "grids": grids}}
+    print(json.dumps(out), flush=True)
+
+
 def cpu_baseline(wl, n_src: int, R: int = 32) -> dict:
     """The CPU oracle as it stands (single-threaded C, FP64 block traversal) on a bounded
     sample of the workload: `n_src` sources (their states from the oracle's own state
@@ -537,9 +606,10 @@ def main():
     ap.add_argument("--sources", type=int, default=0, help="use only the first K sources (small profiling case)")
     ap.add_argument("--state-cache", default="", help="load/save the solved states (.npy) to skip the state solve")
     ap.add_argument("--gn-max-iters", type=int, default=300)
-    ap.add_argument("--workload", choices=["apply", "lsqr", "gn"], default="apply",
+    ap.add_argument("--workload", choices=["apply", "lsqr", "gn", "stress"], default="apply",
                     help="apply: the benchmark line (3-D apply config); lsqr: the 20-iteration Krylov config; "
-                         "gn: LSMR on the augmented Gauss-Newton operator (Sec. 4.5)")
+                         "gn: LSMR on the augmented Gauss-Newton operator (Sec. 4.5); "
+                         "stress: the three steep-hill grids with right-hand-side chunking")
     ap.add_argument("--lsqr-dtype", choices=["f64", "f32"], default="f64")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
@@ -550,6 +620,8 @@ def main():
         run_lsqr(args)
     elif args.workload == "gn":
         run_gn(args)
+    elif args.workload == "stress":
+        run_stress(args)
     else:
         run_ours(args)
 

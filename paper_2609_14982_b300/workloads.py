@@ -369,9 +369,9 @@ def config5_grid(which: int) -> Workload:
     sig = hill_h / (math.sqrt(math.e) * math.tan(math.radians(55.0)))
     g, slope = _config3d("3d", n, L, H, 2.0, seed, hill_h=hill_h, hill_sigma=sig)
     v = _velocity3d(g, 2.0)
-    side = int(round(math.sqrt(S)))
-    ia = np.linspace(5, n[0] - 6, side).round().astype(int)
-    ib = np.linspace(5, n[1] - 6, S // side).round().astype(int)
+    na = 1 << int(math.floor(math.log2(math.sqrt(S))))   # lattice na x (S / na): 4 x 8 or 8 x 8
+    ia = np.linspace(5, n[0] - 6, na).round().astype(int)
+    ib = np.linspace(5, n[1] - 6, S // na).round().astype(int)
     src = np.array([_surface_index(g, a, b) for a in ia for b in ib], dtype=np.int32)
     rec = np.array([_surface_index(g, a, b) for a in range(2, n[0], 5) for b in range(2, n[1], 5)],
                    dtype=np.int32)
