@@ -123,6 +123,26 @@ __device__ __forceinline__ double lf_update_f32(const LFParams &P, long long a, 
     return (double)(num / den);
 }
 
+// max |d tau| of the warp's lanes into dmax[key]: one atomic per warp when all lanes
+// work for the same source (the common case), else one per lane.  Every lane of the warp
+// must call it (lanes without an update pass key = -1).  Same-address atomics serialise
+// in L2, so one atomic per update made them the cost of a hyperplane launch.
+__device__ __forceinline__ void warp_max_into(unsigned long long *dmax, int key, double dd)
+{
+    const unsigned full = 0xffffffffu;
+    unsigned long long bits = key >= 0 ? (unsigned long long)__double_as_longlong(dd) : 0ull;
+    const int k0 = __shfl_sync(full, key, 0);
+    if (__all_sync(full, key == k0 || key < 0) && k0 >= 0) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(full, bits, o);
+            bits = other > bits ? other : bits;   // non-negative doubles order like their bits
+        }
+        if ((threadIdx.x & 31) == 0) atomicMax(dmax + k0, bits);
+    } else if (key >= 0) {
+        atomicMax(dmax + key, bits);
+    }
+}
+
 __global__ void k_lf_plane(LFParams P)
 {
     const GridDesc &g = P.g;
@@ -131,57 +151,67 @@ __global__ void k_lf_plane(LFParams P)
     const int m0 = g.n[0] - 2, m1 = g.n[1] - 2, m2 = nd == 3 ? g.n[2] - 2 : 1;
     long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long span = (long long)(P.hi0 - P.lo0 + 1) * (nd == 3 ? m1 : 1);
-    if (tid >= span * P.S) return;
-    long long a = tid / span, cell = tid - a * span;
-    if (!P.active[a]) return;
-    int c0, c1, c2;
+    bool valid = tid < span * P.S;
+    long long a = valid ? tid / span : 0, cell = tid - a * span;
+    valid = valid && P.active[a];
+    int c0 = 0, c1 = 0, c2 = 0;
     if (nd == 3) {
         c0 = P.lo0 + (int)(cell / m1);
         c1 = (int)(cell % m1);
         c2 = P.h - c0 - c1;
-        if (c2 < 0 || c2 >= m2) return;
+        valid = valid && c2 >= 0 && c2 < m2;
     } else {
         c0 = P.lo0 + (int)cell;
         c1 = P.h - c0;
-        c2 = 0;
-        if (c1 < 0 || c1 >= m1) return;
+        valid = valid && c1 >= 0 && c1 < m1;
     }
-    int i0 = 1 + ((P.order & 1) ? m0 - 1 - c0 : c0);
-    int i1 = 1 + ((P.order & 2) ? m1 - 1 - c1 : c1);
-    int i2 = nd == 3 ? 1 + ((P.order & 4) ? m2 - 1 - c2 : c2) : 0;
-    long long i = nd == 3 ? ((long long)i0 * g.n[1] + i1) * g.n[2] + i2 : (long long)i0 * g.n[1] + i1;
-    long long v = a * g.N + i;
-    if (P.fixed[v]) return;
-    int c[3] = {i0, i1, i2};
-    double nv = (P.fp32 && P.T0[v] > P.t0_fp64[a]) ? lf_update_f32(P, a, i) : lf_update(P, a, i, c);
-    double old = P.tau[v];
-    P.tau[v] = nv;
-    double dd = fabs(nv - old);
-    atomicMax(P.dmax + a, (unsigned long long)__double_as_longlong(dd));
+    long long v = 0;
+    double dd = 0.0;
+    if (valid) {
+        const int i0 = 1 + ((P.order & 1) ? m0 - 1 - c0 : c0);
+        const int i1 = 1 + ((P.order & 2) ? m1 - 1 - c1 : c1);
+        const int i2 = nd == 3 ? 1 + ((P.order & 4) ? m2 - 1 - c2 : c2) : 0;
+        const long long i = nd == 3 ? ((long long)i0 * g.n[1] + i1) * g.n[2] + i2 : (long long)i0 * g.n[1] + i1;
+        v = a * g.N + i;
+        valid = !P.fixed[v];
+        if (valid) {
+            int c[3] = {i0, i1, i2};
+            const double nv = (P.fp32 && P.T0[v] > P.t0_fp64[a]) ? lf_update_f32(P, a, i) : lf_update(P, a, i, c);
+            const double old = P.tau[v];
+            P.tau[v] = nv;
+            dd = fabs(nv - old);
+        }
+    }
+    warp_max_into(P.dmax, valid ? (int)a : -1, dd);
 }
 
 // boundary nodes take the value of the nearest interior node along the inward diagonal
 __global__ void k_lf_boundary(GridDesc g, int S, const unsigned char *__restrict__ fixed,
                               const unsigned char *__restrict__ active, double *tau, unsigned long long *dmax)
 {
-    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (v >= g.N * S || fixed[v]) return;
-    long long a = v / g.N, i = v - a * g.N;
-    if (!active[a]) return;
-    int c[3];
-    if (g.ndim == 3) { c[2] = (int)(i % g.n[2]); c[1] = (int)((i / g.n[2]) % g.n[1]); c[0] = (int)(i / g.st[0]); }
-    else { c[1] = (int)(i % g.n[1]); c[0] = (int)(i / g.n[1]); c[2] = 0; }
-    long long step = 0;
-    for (int d = 0; d < g.ndim; ++d) {
-        if (c[d] == 0) step += g.st[d];
-        else if (c[d] == g.n[d] - 1) step -= g.st[d];
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    bool valid = v < g.N * S && !fixed[v];
+    const long long a = valid ? v / g.N : 0, i = v - a * g.N;
+    valid = valid && active[a];
+    double dd = 0.0;
+    if (valid) {
+        int c[3];
+        if (g.ndim == 3) { c[2] = (int)(i % g.n[2]); c[1] = (int)((i / g.n[2]) % g.n[1]); c[0] = (int)(i / g.st[0]); }
+        else { c[1] = (int)(i % g.n[1]); c[0] = (int)(i / g.n[1]); c[2] = 0; }
+        long long step = 0;
+        for (int d = 0; d < g.ndim; ++d) {
+            if (c[d] == 0) step += g.st[d];
+            else if (c[d] == g.n[d] - 1) step -= g.st[d];
+        }
+        valid = step != 0;
+        if (valid) {
+            double *ta = tau + a * g.N;
+            const double nv = ta[i + step];
+            dd = fabs(nv - ta[i]);
+            ta[i] = nv;
+        }
     }
-    if (step == 0) return;
-    double *ta = tau + a * g.N;
-    double nv = ta[i + step];
-    double dd = fabs(nv - ta[i]);
-    ta[i] = nv;
-    atomicMax(dmax + a, (unsigned long long)__double_as_longlong(dd));
+    warp_max_into(dmax, valid ? (int)a : -1, dd);
 }
 
 // T0 beyond which a node of source a is far enough from it for FP32 arithmetic
@@ -195,6 +225,82 @@ __global__ void k_eik_out(long long SN, const double *T0, const double *tau, dou
 {
     long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (v < SN) T[v] = T0[v] * tau[v];
+}
+
+// One LF cycle: the 2^ndim orderings, each a sequence of hyperplane launches (a plane's
+// nodes only read the previous plane's values: Gauss-Seidel order) and the boundary copy.
+static void lf_cycle_launch(LFParams P, long long SN, int m0, int m1, int hmax_i, int nord, cudaStream_t st)
+{
+    const int nd = P.g.ndim;
+    cudaMemsetAsync(P.dmax, 0, P.S * sizeof(unsigned long long), st);
+    for (int o = 0; o < nord; ++o) {
+        P.order = o;
+        for (int h = 0; h <= hmax_i; ++h) {
+            P.h = h;
+            const int rest = hmax_i - (m0 - 1);
+            P.lo0 = std::max(0, h - rest);
+            P.hi0 = std::min(m0 - 1, h);
+            const long long span = (long long)(P.hi0 - P.lo0 + 1) * (nd == 3 ? m1 : 1) * P.S;
+            k_lf_plane<<<(unsigned)((span + 255) / 256), 256, 0, st>>>(P);
+        }
+        k_lf_boundary<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(P.g, P.S, P.fixed, P.active, P.tau, P.dmax);
+    }
+}
+
+// Cycles until every source's largest change over a cycle is below tol (each source
+// stops iterating at its own first such cycle).  With use_graph the thousands of
+// launches of one cycle are captured once (on a private stream) and replayed per cycle.
+static cudaError_t lf_cycles(LFParams P, int S, long long SN, int m0, int m1, int hmax_i, int nord, double tol,
+                             int max_cycles, bool use_graph, int *used, cudaStream_t st)
+{
+    std::vector<unsigned char> h_active(S, 1);
+    std::vector<unsigned long long> h_dmax(S);
+    cudaError_t e = cudaMemcpyAsync((void *)P.active, h_active.data(), S, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto cleanup = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap) cudaStreamDestroy(cap);
+    };
+    if (use_graph) {
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            lf_cycle_launch(P, SN, m0, m1, hmax_i, nord, cap);
+            e = cudaStreamEndCapture(cap, &graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) { cleanup(); return e; }
+    }
+    int left = S;
+    *used = -1;
+    for (int cyc = 1; cyc <= max_cycles; ++cyc) {
+        if (use_graph) e = cudaGraphLaunch(exec, st);
+        else {
+            lf_cycle_launch(P, SN, m0, m1, hmax_i, nord, st);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_dmax.data(), P.dmax, S * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { cleanup(); return e; }
+        bool changed = false;
+        for (int a = 0; a < S; ++a) {
+            if (!h_active[a]) continue;
+            double dm;
+            std::memcpy(&dm, &h_dmax[a], sizeof dm);
+            if (dm < tol) { h_active[a] = 0; --left; changed = true; }
+        }
+        if (left == 0) { *used = cyc; break; }
+        if (changed) {
+            e = cudaMemcpyAsync((void *)P.active, h_active.data(), S, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) { cleanup(); return e; }
+        }
+    }
+    cleanup();
+    return cudaSuccess;
 }
 
 }  // namespace eik
@@ -258,38 +364,8 @@ extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const in
         const int hmax_i = (m0 - 1) + (m1 - 1) + (nd == 3 ? m2 - 1 : 0);
         const int nord = 1 << nd;
         // each source stops at the first cycle whose largest change is below eik_tol
-        std::vector<unsigned char> h_active(S, 1);
-        std::vector<unsigned long long> h_dmax(S);
-        TRY(cudaMemcpyAsync(active, h_active.data(), S, cudaMemcpyHostToDevice, st));
-        int used = -1, left = S;
-        for (int cyc = 1; cyc <= opts->eik_max_cycles; ++cyc) {
-            TRY(cudaMemsetAsync(dmax, 0, S * sizeof(unsigned long long), st));
-            for (int o = 0; o < nord; ++o) {
-                P.order = o;
-                for (int h = 0; h <= hmax_i; ++h) {
-                    P.h = h;
-                    int rest = hmax_i - (m0 - 1);
-                    P.lo0 = std::max(0, h - rest);
-                    P.hi0 = std::min(m0 - 1, h);
-                    long long span = (long long)(P.hi0 - P.lo0 + 1) * (nd == 3 ? m1 : 1) * S;
-                    k_lf_plane<<<(unsigned)((span + 255) / 256), 256, 0, st>>>(P);
-                }
-                k_lf_boundary<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(g, S, fixed, active, tau, dmax);
-            }
-            TRY(cudaGetLastError());
-            TRY(cudaMemcpyAsync(h_dmax.data(), dmax, S * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-            TRY(cudaStreamSynchronize(st));
-            bool changed = false;
-            for (int a = 0; a < S; ++a) {
-                if (!h_active[a]) continue;
-                double dm;
-                std::memcpy(&dm, &h_dmax[a], sizeof dm);
-                if (dm < tol) { h_active[a] = 0; --left; changed = true; }
-            }
-            if (left == 0) { used = cyc; break; }
-            (void)0;
-            if (changed) TRY(cudaMemcpyAsync(active, h_active.data(), S, cudaMemcpyHostToDevice, st));
-        }
+        int used = -1;
+        TRY(lf_cycles(P, S, SN, m0, m1, hmax_i, nord, tol, opts->eik_max_cycles, true, &used, st));
         k_eik_out<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(SN, T0, tau, T);
         TRY(cudaGetLastError());
         TRY(cudaStreamSynchronize(st));
@@ -423,39 +499,10 @@ extern "C" int eik_forward_noalloc(const eik_grid *gin, const double *s, int S, 
         const int m0 = g.n[0] - 2, m1 = g.n[1] - 2, m2 = nd == 3 ? g.n[2] - 2 : 1;
         const int hmax_i = (m0 - 1) + (m1 - 1) + (nd == 3 ? m2 - 1 : 0);
         const int nord = 1 << nd;
-        // each source stops at the first cycle whose largest change is below eik_tol
-        std::vector<unsigned char> h_active(S, 1);
-        std::vector<unsigned long long> h_dmax(S);
-        TRY(cudaMemcpyAsync(active, h_active.data(), S, cudaMemcpyHostToDevice, st));
-        int used = -1, left = S;
-        for (int cyc = 1; cyc <= opts->eik_max_cycles; ++cyc) {
-            TRY(cudaMemsetAsync(dmax, 0, S * sizeof(unsigned long long), st));
-            for (int o = 0; o < nord; ++o) {
-                P.order = o;
-                for (int h = 0; h <= hmax_i; ++h) {
-                    P.h = h;
-                    int rest = hmax_i - (m0 - 1);
-                    P.lo0 = std::max(0, h - rest);
-                    P.hi0 = std::min(m0 - 1, h);
-                    long long span = (long long)(P.hi0 - P.lo0 + 1) * (nd == 3 ? m1 : 1) * S;
-                    k_lf_plane<<<(unsigned)((span + 255) / 256), 256, 0, st>>>(P);
-                }
-                k_lf_boundary<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(g, S, fixed, active, tau, dmax);
-            }
-            TRY(cudaGetLastError());
-            TRY(cudaMemcpyAsync(h_dmax.data(), dmax, S * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-            TRY(cudaStreamSynchronize(st));
-            bool changed = false;
-            for (int a = 0; a < S; ++a) {
-                if (!h_active[a]) continue;
-                double dm;
-                std::memcpy(&dm, &h_dmax[a], sizeof dm);
-                if (dm < tol) { h_active[a] = 0; --left; changed = true; }
-            }
-            if (left == 0) { used = cyc; break; }
-            (void)0;
-            if (changed) TRY(cudaMemcpyAsync(active, h_active.data(), S, cudaMemcpyHostToDevice, st));
-        }
+        // each source stops at the first cycle whose largest change is below eik_tol; direct
+        // launches (a graph would be one more object to create)
+        int used = -1;
+        TRY(lf_cycles(P, S, SN, m0, m1, hmax_i, nord, tol, opts->eik_max_cycles, false, &used, st));
         k_eik_out<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(SN, T0, tau, T);
         TRY(cudaGetLastError());
         TRY(cudaStreamSynchronize(st));
