@@ -28,6 +28,12 @@ namespace eik {
 
 __global__ void k_metric(GridDesc g, const double *__restrict__ xyz, double *__restrict__ G, double *__restrict__ Jout);
 
+// The per-(source, node) arrays of the LF solve (T0, g0, alpha, tau, fixed) are stored
+// node-major, v = i * S + a: the threads of a hyperplane launch take the sources of a
+// node as their fastest index, so their loads of a node's (and its neighbours') values
+// are contiguous across the warp.
+constexpr int DSLOTS = 1024;   // convergence maxima per source, spread over this many words
+
 // per (source, node): T0, g0 = J^T grad_x T0, alpha_d, fixed flag
 __global__ void k_eik_prep(GridDesc g, int S, const double *__restrict__ xyz, const double *__restrict__ Jm,
                            const double *__restrict__ G, const double *__restrict__ s, const int *__restrict__ src,
@@ -36,7 +42,7 @@ __global__ void k_eik_prep(GridDesc g, int S, const double *__restrict__ xyz, co
     long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (v >= g.N * S) return;
     const int nd = g.ndim;
-    long long a = v / g.N, i = v - a * g.N;
+    long long i = v / S, a = v - i * S;
     long long k = src[a];
     double ss = s[k];
     double d[3], r2 = 0.0;
@@ -64,19 +70,19 @@ struct LFParams {
     const unsigned char *fixed;
     const unsigned char *active;   // [S] sources still iterating
     double *tau;
-    unsigned long long *dmax;   // [S] bit pattern of max |d tau| per source (non-negative double)
+    unsigned long long *dmax;   // [S][DSLOTS] bit patterns of max |d tau| (non-negative doubles)
 };
 
 __device__ __forceinline__ double lf_update(const LFParams &P, long long a, long long i, const int *c)
 {
     const GridDesc &g = P.g;
     const int nd = g.ndim;
-    const long long v = a * g.N + i;
-    const double *tau = P.tau + a * g.N;
+    const long long S = P.S, v = i * S + a;
+    const double *tau = P.tau + a;   // node j of source a at tau[j * S]
     const double T0 = P.T0[v];
-    const double ti = tau[i];
+    const double ti = tau[i * S];
     double p[3], Pv[3];
-    for (int d = 0; d < nd; ++d) p[d] = (tau[i + g.st[d]] - tau[i - g.st[d]]) / (2.0 * g.dxi[d]);
+    for (int d = 0; d < nd; ++d) p[d] = (tau[(i + g.st[d]) * S] - tau[(i - g.st[d]) * S]) / (2.0 * g.dxi[d]);
     for (int b = 0; b < nd; ++b) Pv[b] = ti * P.g0[v * nd + b] + T0 * p[b];
     double H2 = 0.0;
     for (int x = 0; x < nd; ++x) {
@@ -88,7 +94,7 @@ __device__ __forceinline__ double lf_update(const LFParams &P, long long a, long
     double num = P.s[i] - H, den = 0.0;
     for (int d = 0; d < nd; ++d) {
         double al = P.alpha[v * nd + d];
-        num = num + al * (tau[i + g.st[d]] + tau[i - g.st[d]]) / (2.0 * g.dxi[d]);
+        num = num + al * (tau[(i + g.st[d]) * S] + tau[(i - g.st[d]) * S]) / (2.0 * g.dxi[d]);
         den = den + al / g.dxi[d];
     }
     (void)c;
@@ -100,13 +106,13 @@ __device__ __forceinline__ double lf_update_f32(const LFParams &P, long long a, 
 {
     const GridDesc &g = P.g;
     const int nd = g.ndim;
-    const long long v = a * g.N + i;
-    const double *tau = P.tau + a * g.N;
+    const long long S = P.S, v = i * S + a;
+    const double *tau = P.tau + a;
     const float T0 = (float)P.T0[v];
-    const float ti = (float)tau[i];
+    const float ti = (float)tau[i * S];
     float p[3], Pv[3];
     for (int d = 0; d < nd; ++d)
-        p[d] = ((float)tau[i + g.st[d]] - (float)tau[i - g.st[d]]) / (2.0f * (float)g.dxi[d]);
+        p[d] = ((float)tau[(i + g.st[d]) * S] - (float)tau[(i - g.st[d]) * S]) / (2.0f * (float)g.dxi[d]);
     for (int b = 0; b < nd; ++b) Pv[b] = ti * (float)P.g0[v * nd + b] + T0 * p[b];
     float H2 = 0.0f;
     for (int x = 0; x < nd; ++x) {
@@ -117,18 +123,20 @@ __device__ __forceinline__ double lf_update_f32(const LFParams &P, long long a, 
     float num = (float)P.s[i] - sqrtf(H2), den = 0.0f;
     for (int d = 0; d < nd; ++d) {
         const float al = (float)P.alpha[v * nd + d];
-        num = num + al * ((float)tau[i + g.st[d]] + (float)tau[i - g.st[d]]) / (2.0f * (float)g.dxi[d]);
+        num = num + al * ((float)tau[(i + g.st[d]) * S] + (float)tau[(i - g.st[d]) * S]) / (2.0f * (float)g.dxi[d]);
         den = den + al / (float)g.dxi[d];
     }
     return (double)(num / den);
 }
 
-// max |d tau| of the warp's lanes into dmax[key]: one atomic per warp when all lanes
-// work for the same source (the common case), else one per lane.  Every lane of the warp
-// must call it (lanes without an update pass key = -1).  Same-address atomics serialise
-// in L2, so one atomic per update made them the cost of a hyperplane launch.
+// max |d tau| of the warp's lanes into source key's word of this block's slot: one atomic
+// per warp when all lanes work for the same source, else one per lane, spread over
+// DSLOTS words per source.  Every lane of the warp must call it (lanes without an update
+// pass key = -1).  Same-address atomics serialise in L2; one word per source made them
+// the cost of a hyperplane launch.
 __device__ __forceinline__ void warp_max_into(unsigned long long *dmax, int key, double dd)
 {
+    dmax += blockIdx.x & (DSLOTS - 1);
     const unsigned full = 0xffffffffu;
     unsigned long long bits = key >= 0 ? (unsigned long long)__double_as_longlong(dd) : 0ull;
     const int k0 = __shfl_sync(full, key, 0);
@@ -137,9 +145,9 @@ __device__ __forceinline__ void warp_max_into(unsigned long long *dmax, int key,
             const unsigned long long other = __shfl_xor_sync(full, bits, o);
             bits = other > bits ? other : bits;   // non-negative doubles order like their bits
         }
-        if ((threadIdx.x & 31) == 0) atomicMax(dmax + k0, bits);
+        if ((threadIdx.x & 31) == 0) atomicMax(dmax + (long long)k0 * DSLOTS, bits);
     } else if (key >= 0) {
-        atomicMax(dmax + key, bits);
+        atomicMax(dmax + (long long)key * DSLOTS, bits);
     }
 }
 
@@ -152,7 +160,7 @@ __global__ void k_lf_plane(LFParams P)
     long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long span = (long long)(P.hi0 - P.lo0 + 1) * (nd == 3 ? m1 : 1);
     bool valid = tid < span * P.S;
-    long long a = valid ? tid / span : 0, cell = tid - a * span;
+    long long cell = valid ? tid / P.S : 0, a = tid - cell * P.S;   // sources fastest
     valid = valid && P.active[a];
     int c0 = 0, c1 = 0, c2 = 0;
     if (nd == 3) {
@@ -172,7 +180,7 @@ __global__ void k_lf_plane(LFParams P)
         const int i1 = 1 + ((P.order & 2) ? m1 - 1 - c1 : c1);
         const int i2 = nd == 3 ? 1 + ((P.order & 4) ? m2 - 1 - c2 : c2) : 0;
         const long long i = nd == 3 ? ((long long)i0 * g.n[1] + i1) * g.n[2] + i2 : (long long)i0 * g.n[1] + i1;
-        v = a * g.N + i;
+        v = i * P.S + a;
         valid = !P.fixed[v];
         if (valid) {
             int c[3] = {i0, i1, i2};
@@ -191,7 +199,7 @@ __global__ void k_lf_boundary(GridDesc g, int S, const unsigned char *__restrict
 {
     const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     bool valid = v < g.N * S && !fixed[v];
-    const long long a = valid ? v / g.N : 0, i = v - a * g.N;
+    const long long i = valid ? v / S : 0, a = v - i * S;
     valid = valid && active[a];
     double dd = 0.0;
     if (valid) {
@@ -205,10 +213,9 @@ __global__ void k_lf_boundary(GridDesc g, int S, const unsigned char *__restrict
         }
         valid = step != 0;
         if (valid) {
-            double *ta = tau + a * g.N;
-            const double nv = ta[i + step];
-            dd = fabs(nv - ta[i]);
-            ta[i] = nv;
+            const double nv = tau[(i + step) * S + a];
+            dd = fabs(nv - tau[v]);
+            tau[v] = nv;
         }
     }
     warp_max_into(dmax, valid ? (int)a : -1, dd);
@@ -221,10 +228,29 @@ __global__ void k_t0_threshold(int S, const double *__restrict__ s, const int *_
     if (a < S) out[a] = s[src[a]] * dist;
 }
 
-__global__ void k_eik_out(long long SN, const double *T0, const double *tau, double *T)
+// T [S][N] (source-major, the caller's layout) from the node-major T0 and tau
+__global__ void k_eik_out(long long N, int S, const double *T0, const double *tau, double *T)
 {
-    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (v < SN) T[v] = T0[v] * tau[v];
+    const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (o >= N * S) return;
+    const long long a = o / N, i = o - a * N, v = i * S + a;
+    T[o] = T0[v] * tau[v];
+}
+
+// max over the DSLOTS words of each source into its first word
+__global__ void k_dmax_fold(unsigned long long *dmax)
+{
+    __shared__ unsigned long long red[256];
+    unsigned long long *w = dmax + (long long)blockIdx.x * DSLOTS;
+    unsigned long long m = 0;
+    for (int k = threadIdx.x; k < DSLOTS; k += blockDim.x) m = w[k] > m ? w[k] : m;
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h && red[threadIdx.x + h] > red[threadIdx.x]) red[threadIdx.x] = red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) w[0] = red[0];
 }
 
 // One LF cycle: the 2^ndim orderings, each a sequence of hyperplane launches (a plane's
@@ -232,7 +258,7 @@ __global__ void k_eik_out(long long SN, const double *T0, const double *tau, dou
 static void lf_cycle_launch(LFParams P, long long SN, int m0, int m1, int hmax_i, int nord, cudaStream_t st)
 {
     const int nd = P.g.ndim;
-    cudaMemsetAsync(P.dmax, 0, P.S * sizeof(unsigned long long), st);
+    cudaMemsetAsync(P.dmax, 0, (size_t)P.S * DSLOTS * sizeof(unsigned long long), st);
     for (int o = 0; o < nord; ++o) {
         P.order = o;
         for (int h = 0; h <= hmax_i; ++h) {
@@ -245,6 +271,7 @@ static void lf_cycle_launch(LFParams P, long long SN, int m0, int m1, int hmax_i
         }
         k_lf_boundary<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(P.g, P.S, P.fixed, P.active, P.tau, P.dmax);
     }
+    k_dmax_fold<<<P.S, 256, 0, st>>>(P.dmax);
 }
 
 // Cycles until every source's largest change over a cycle is below tol (each source
@@ -283,7 +310,9 @@ static cudaError_t lf_cycles(LFParams P, int S, long long SN, int m0, int m1, in
             lf_cycle_launch(P, SN, m0, m1, hmax_i, nord, st);
             e = cudaGetLastError();
         }
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h_dmax.data(), P.dmax, S * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(h_dmax.data(), sizeof(unsigned long long), P.dmax, DSLOTS * sizeof(unsigned long long),
+                                  sizeof(unsigned long long), S, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { cleanup(); return e; }
         bool changed = false;
@@ -344,7 +373,7 @@ extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const in
         TRY(cudaMalloc(&tau, SN * sizeof(double)));
         TRY(cudaMalloc(&fixed, SN));
         TRY(cudaMalloc(&src_d, S * sizeof(int)));
-        TRY(cudaMalloc(&dmax, S * sizeof(unsigned long long)));
+        TRY(cudaMalloc(&dmax, (size_t)S * DSLOTS * sizeof(unsigned long long)));
         TRY(cudaMalloc(&active, S));
         TRY(cudaMalloc(&t0_fp64, S * sizeof(double)));
         TRY(cudaMemcpyAsync(src_d, src_node, S * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -366,7 +395,7 @@ extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const in
         // each source stops at the first cycle whose largest change is below eik_tol
         int used = -1;
         TRY(lf_cycles(P, S, SN, m0, m1, hmax_i, nord, tol, opts->eik_max_cycles, true, &used, st));
-        k_eik_out<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(SN, T0, tau, T);
+        k_eik_out<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(N, S, T0, tau, T);
         TRY(cudaGetLastError());
         TRY(cudaStreamSynchronize(st));
 #undef TRY
@@ -413,7 +442,7 @@ size_t noalloc_bytes(int nd, long long N, int S)
     b += align256((size_t)SN * sizeof(double));              // tau
     b += align256((size_t)SN);                               // fixed flags
     b += align256((size_t)S * sizeof(int));                  // source nodes
-    b += align256((size_t)S * sizeof(unsigned long long));   // max change per source
+    b += align256((size_t)S * DSLOTS * sizeof(unsigned long long));   // max change per source
     b += align256((size_t)S);                                // active flags
     b += align256((size_t)S * sizeof(double));               // FP32 thresholds
     return b;
@@ -476,7 +505,7 @@ extern "C" int eik_forward_noalloc(const eik_grid *gin, const double *s, int S, 
         double *tau = (double *)carve((size_t)SN * sizeof(double));
         unsigned char *fixed = carve((size_t)SN);
         int *src_d = (int *)carve((size_t)S * sizeof(int));
-        unsigned long long *dmax = (unsigned long long *)carve((size_t)S * sizeof(unsigned long long));
+        unsigned long long *dmax = (unsigned long long *)carve((size_t)S * DSLOTS * sizeof(unsigned long long));
         unsigned char *active = carve((size_t)S);
         double *t0_fp64 = (double *)carve((size_t)S * sizeof(double));
         cudaStream_t st = (cudaStream_t)stream;
@@ -503,7 +532,7 @@ extern "C" int eik_forward_noalloc(const eik_grid *gin, const double *s, int S, 
         // launches (a graph would be one more object to create)
         int used = -1;
         TRY(lf_cycles(P, S, SN, m0, m1, hmax_i, nord, tol, opts->eik_max_cycles, false, &used, st));
-        k_eik_out<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(SN, T0, tau, T);
+        k_eik_out<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(N, S, T0, tau, T);
         TRY(cudaGetLastError());
         TRY(cudaStreamSynchronize(st));
 #undef TRY
