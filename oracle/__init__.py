@@ -17,6 +17,7 @@ What it computes (paper sections in brackets):
   * directional sweeping (Gauss-Seidel over 2^D orderings)            [Sec. 3.6]
   * the augmented Gauss-Newton operator K, K^T (W_d, roughness R,
     relative damping S_k) and LSMR on it                               [Sec. 4.5]
+  * the node <- cell averaging map of a cell-based velocity model      [Sec. 5.3]
 
 Where the paper leaves a detail open the oracle takes one stated reading (face
 averages, boundary stencils, canonical order); those readings are pinned by the
@@ -508,3 +509,29 @@ def lsmr(apply_A, apply_AT, b: np.ndarray, iters: int):
     info = {"normr": float(normr), "normar": float(abs(zetabar)), "norma": float(np.sqrt(norma2)),
             "normx": float(np.linalg.norm(x)), "iters": iters}
     return x, info
+
+
+# --------------------------------------------------------------------------- cell model
+def cell_average(grid):
+    """Node <- cell map of a cell-based velocity model (the paper's inversion cells,
+    Sec. 5.3: one cell per grid hexahedron).  Reading (the paper gives no formula): a
+    node's velocity perturbation is the mean of its adjacent cells' perturbations,
+    dv_node[j] = (1 / n_adj(j)) sum over the cells c with j as a corner of dv_cell[c].
+    Cells are indexed like nodes on the grid of extents n_d - 1.  Returns a scipy.sparse
+    CSR matrix [N, n_cells]; the model map of J is then M = -s^2 (velocity) times it."""
+    import itertools
+
+    import scipy.sparse as sp
+    n = tuple(int(x) for x in grid.n[:grid.ndim])
+    m = tuple(x - 1 for x in n)
+    nc = int(np.prod(m))
+    cidx = np.arange(nc).reshape(m)
+    rows, cols = [], []
+    for off in itertools.product((0, 1), repeat=len(n)):
+        sl = tuple(slice(o, o + mm) for o, mm in zip(off, m))
+        nodes = np.arange(int(np.prod(n))).reshape(n)[sl]
+        rows.append(nodes.ravel())
+        cols.append(cidx.ravel())
+    rows, cols = np.concatenate(rows), np.concatenate(cols)
+    nadj = np.bincount(rows, minlength=int(np.prod(n))).astype(np.float64)
+    return sp.csr_matrix((1.0 / nadj[rows], (rows, cols)), shape=(int(np.prod(n)), nc))
