@@ -313,6 +313,23 @@ int lsqr_solution(eik_lsqr *l, void *x, double *scalars, eik_stream stream);
 void lsqr_free(eik_lsqr *l);
 
 /*
+ * Cell-based velocity model (the inversion cells of Sec. 5.3, one per grid hexahedron,
+ * indexed like nodes on the grid of extents n_d - 1).  The paper gives no formula for the
+ * cell-to-node map; reading: a node's perturbation is the mean over its adjacent cells.
+ * A Jacobian action on cells is then J (A p_cell) with the tangent's velocity model map,
+ * and its transpose A^T (J^T y).
+ *   model_cells_to_nodes  p_node[j][r] = mean over the cells c adjacent to node j of
+ *                         p_cell[c][r]   (device [n_cells][R] -> device [N][R])
+ *   model_nodes_to_cells  the transpose: g_cell[c][r] = sum over the corner nodes j of c
+ *                         of g_node[j][r] / (number of cells adjacent to j)
+ *                         (device [N][R] -> device [n_cells][R])
+ * g: only ndim and n are read (each n_d >= 2); dtype EIK_F32 or EIK_F64 (sums in FP64);
+ * asynchronous on stream; both are gathers (deterministic).
+ */
+int model_cells_to_nodes(const eik_grid *g, const void *p_cell, int R, void *p_node, int dtype, eik_stream stream);
+int model_nodes_to_cells(const eik_grid *g, const void *g_node, int R, void *g_cell, int dtype, eik_stream stream);
+
+/*
  * The augmented Gauss-Newton operator of Sec. 4.5 (Eq. augmented-ls, Eq.
  * augmented-actions) on a built tangent, one model vector:
  *   K p   = [ W_d J p ; lambda R p ; lambda S p ]              S = gamma diag(1 / v_k)

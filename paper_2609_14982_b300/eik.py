@@ -27,7 +27,7 @@ EXPORTED = ["eik_opts_default", "eik_last_error", "eik_version", "eik_forward", 
             "lsqr_create", "lsqr_start", "lsqr_iterate", "lsqr_solution", "lsqr_free",
             "eik_forward_noalloc", "eik_forward_noalloc_capacity",
             "gn_create", "gn_dims", "gn_apply", "gn_apply_T", "gn_lsmr_start", "gn_lsmr_iterate",
-            "gn_lsmr_solution", "gn_free"]
+            "gn_lsmr_solution", "gn_free", "model_cells_to_nodes", "model_nodes_to_cells"]
 
 
 class EikError(RuntimeError):
@@ -102,6 +102,8 @@ def lib():
         L.gn_lsmr_solution.argtypes = [P, P, P, P]
         L.gn_free.argtypes = [P]
         L.gn_free.restype = None
+        L.model_cells_to_nodes.argtypes = [C.POINTER(Grid_), P, I, P, I, P]
+        L.model_nodes_to_cells.argtypes = [C.POINTER(Grid_), P, I, P, I, P]
         L.sweep_apply.argtypes = [P, I, P, I, P, I, C.POINTER(Opts), C.POINTER(I), P]
         _lib = L
     return _lib
@@ -159,6 +161,31 @@ class DeviceGrid:
             self.c.n[d] = grid.n[d] if d < grid.ndim else 1
             self.c.dxi[d] = grid.dxi[d] if d < grid.ndim else 1.0
         self.c.xyz = self.xyz.data_ptr()
+
+
+def n_cells(dgrid: DeviceGrid) -> int:
+    out = 1
+    for m in dgrid.n[:dgrid.ndim]:
+        out *= m - 1
+    return out
+
+
+def cells_to_nodes(dgrid: DeviceGrid, p_cell: torch.Tensor) -> torch.Tensor:
+    """Node perturbations [N, R] from cell perturbations [n_cells, R] (mean over adjacent cells)."""
+    pc = p_cell if p_cell.dim() == 2 else p_cell[:, None]
+    out = torch.empty((dgrid.N, pc.shape[1]), dtype=pc.dtype, device=pc.device)
+    _check(lib().model_cells_to_nodes(C.byref(dgrid.c), _dev(pc), int(pc.shape[1]), _dev(out, pc.dtype, "out"),
+                                      _dt(pc.dtype), _stream()))
+    return out if p_cell.dim() == 2 else out[:, 0]
+
+
+def nodes_to_cells(dgrid: DeviceGrid, g_node: torch.Tensor) -> torch.Tensor:
+    """Transpose of cells_to_nodes: [N, R] -> [n_cells, R]."""
+    gn = g_node if g_node.dim() == 2 else g_node[:, None]
+    out = torch.empty((n_cells(dgrid), gn.shape[1]), dtype=gn.dtype, device=gn.device)
+    _check(lib().model_nodes_to_cells(C.byref(dgrid.c), _dev(gn), int(gn.shape[1]), _dev(out, gn.dtype, "out"),
+                                      _dt(gn.dtype), _stream()))
+    return out if g_node.dim() == 2 else out[:, 0]
 
 
 def eik_forward(dgrid: DeviceGrid, s: torch.Tensor, src, opts: Opts | None = None, out: torch.Tensor | None = None):
