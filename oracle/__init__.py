@@ -18,6 +18,7 @@ What it computes (paper sections in brackets):
   * the augmented Gauss-Newton operator K, K^T (W_d, roughness R,
     relative damping S_k) and LSMR on it                               [Sec. 4.5]
   * the node <- cell averaging map of a cell-based velocity model      [Sec. 5.3]
+  * multilinear sampling of off-grid receivers (P, P^T) in J, J^T      [Sec. 4.4]
 
 Where the paper leaves a detail open the oracle takes one stated reading (face
 averages, boundary stencils, canonical order); those readings are pinned by the
@@ -535,3 +536,50 @@ def cell_average(grid):
     rows, cols = np.concatenate(rows), np.concatenate(cols)
     nadj = np.bincount(rows, minlength=int(np.prod(n))).astype(np.float64)
     return sp.csr_matrix((1.0 / nadj[rows], (rows, cols)), shape=(int(np.prod(n)), nc))
+
+
+# --------------------------------------------------------------------------- off-grid receivers
+def receiver_interp(grid, f: np.ndarray):
+    """Multilinear receiver sampling P (Sec. 4.4's P_a for receivers off the grid nodes;
+    the paper gives no formula, reading: multilinear interpolation in logical index space).
+    f: [n_rec, ndim] fractional logical indices, 0 <= f_d <= n_d - 1.  Corner base
+    b_d = min(floor(f_d), n_d - 2), t_d = f_d - b_d, weight of corner o in {0,1}^ndim
+    = prod_d (t_d if o_d else 1 - t_d).  Returns a scipy.sparse CSR matrix [n_rec, N]."""
+    import itertools
+
+    import scipy.sparse as sp
+    f = np.asarray(f, dtype=np.float64)
+    n = np.array(grid.n[:grid.ndim])
+    base = np.minimum(np.floor(f).astype(np.int64), n - 2)
+    t = f - base
+    strides = np.array([int(np.prod(n[d + 1:])) for d in range(grid.ndim)])
+    rows, cols, vals = [], [], []
+    for o in itertools.product((0, 1), repeat=grid.ndim):
+        o = np.array(o)
+        w = np.prod(np.where(o == 1, t, 1.0 - t), axis=1)
+        rows.append(np.arange(len(f)))
+        cols.append(((base + o) * strides).sum(axis=1))
+        vals.append(w)
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(len(f), int(np.prod(n))))
+
+
+def J_interp(tans, s, Ps, p, model=MODEL_SLOWNESS):
+    """J_a p = P_a A_a^-1 C_a M p with a sparse P_a per source (D = 0); p [N, R] shared.
+    Returns [S, n_rec, R]."""
+    m = model_factor(s, model)
+    out = []
+    for t, P in zip(tans, Ps):
+        dT = solve(t, t.cs[:, None] * (m[:, None] * p))
+        out.append(P @ dT)
+    return np.stack(out)
+
+
+def JT_interp(tans, s, Ps, y, model=MODEL_SLOWNESS):
+    """sum_a M^T C^T A_a^-T P_a^T y_a; y [S, n_rec, R].  Returns [N, R]."""
+    m = model_factor(s, model)
+    g = 0.0
+    for a, (t, P) in enumerate(zip(tans, Ps)):
+        lam = solve_T(t, P.T @ y[a])
+        g = g + m[:, None] * t.cs[:, None] * lam
+    return g
