@@ -313,6 +313,27 @@ int lsqr_solution(eik_lsqr *l, void *x, double *scalars, eik_stream stream);
 void lsqr_free(eik_lsqr *l);
 
 /*
+ * Off-grid receivers (Sec. 4.4: P_a samples the transported field at source a's
+ * receivers; D_a = 0 for on-grid sources).  The paper gives no formula for receivers
+ * between nodes; reading: multilinear interpolation in logical index space.
+ *   tangent_set_receivers   f: host [S][n_rec][ndim] fractional logical indices of each
+ *                           source's receivers, 0 <= f_d <= n_d - 1 (corner base
+ *                           min(floor(f_d), n_d - 2)); n_rec = 0 clears them.  Independent
+ *                           of the on-grid receivers given to tangent_build.  Synchronizes
+ *                           the device.  EIK_ERR_INVALID for a coordinate out of range.
+ *   tangent_apply_interp    J p with P = the multilinear sampling: ds device [N][R]
+ *                           (shared_model != 0) or [S][N][R]; d_rec device [S][n_rec][R]
+ *   tangent_apply_interp_T  J^T y = sum_a M^T C^T A_a^-T P_a^T y_a: y device
+ *                           [S][n_rec][R], g device [N][R] (summed over sources)
+ * Both follow rhs_chunk; they use an internal staging buffer of [S][N][chunk] (kept by
+ * the tangent).  EIK_ERR_INVALID when no off-grid receivers are set.
+ */
+int tangent_set_receivers(eik_tangent *t, int n_rec, const double *f);
+int tangent_apply_interp(eik_tangent *t, const void *ds, int shared_model, int R, void *d_rec, int dtype,
+                         eik_stream stream);
+int tangent_apply_interp_T(eik_tangent *t, const void *y, int R, void *g, int dtype, eik_stream stream);
+
+/*
  * Cell-based velocity model (the inversion cells of Sec. 5.3, one per grid hexahedron,
  * indexed like nodes on the grid of extents n_d - 1).  The paper gives no formula for the
  * cell-to-node map; reading: a node's perturbation is the mean over its adjacent cells.

@@ -99,6 +99,32 @@ int tangent_apply_T(eik_tangent *t, const void *y, int R, int sum_sources, void 
     })
 }
 
+int tangent_set_receivers(eik_tangent *t, int n_rec, const double *f)
+{
+    EIK_GUARD({
+        if (!t || n_rec < 0 || (n_rec > 0 && !f)) { eik::set_error("bad tangent_set_receivers arguments"); return EIK_ERR_INVALID; }
+        EIK_CHECK(cudaDeviceSynchronize());
+        return eik::set_receivers_interp(t->impl, n_rec, f);
+    })
+}
+
+int tangent_apply_interp(eik_tangent *t, const void *ds, int shared_model, int R, void *d_rec, int dtype,
+                         eik_stream stream)
+{
+    EIK_GUARD({
+        if (!t || !ds || !d_rec || R <= 0) { eik::set_error("bad tangent_apply_interp arguments"); return EIK_ERR_INVALID; }
+        return eik::apply_interp_entry(t->impl, ds, shared_model, R, d_rec, dtype, (cudaStream_t)stream);
+    })
+}
+
+int tangent_apply_interp_T(eik_tangent *t, const void *y, int R, void *g, int dtype, eik_stream stream)
+{
+    EIK_GUARD({
+        if (!t || !y || !g || R <= 0) { eik::set_error("bad tangent_apply_interp_T arguments"); return EIK_ERR_INVALID; }
+        return eik::apply_interp_T_entry(t->impl, y, R, g, dtype, (cudaStream_t)stream);
+    })
+}
+
 int tangent_solve(eik_tangent *t, const void *q, int R, void *x, int dtype, eik_stream stream)
 {
     EIK_GUARD({

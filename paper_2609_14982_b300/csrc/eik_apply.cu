@@ -1082,6 +1082,36 @@ static int dispatch_v(Tangent *t, TravParams &P, cudaStream_t st)
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
+// g[j][r] (row stride ld_g) = sum over sources of c_a[j] * x_a[j][r] for the w columns the
+// workspace holds (the reverse field of the last traversal, canonical order)
+int source_sum(Tangent *t, int w, void *g, long long ld_g, int dtype, cudaStream_t st)
+{
+    const void *xp = t->ws_vec;
+    const int V = dtype == EIK_F32 ? 4 : 2;
+    const int L = w / V;
+    if (w % V == 0 && ld_g % V == 0 && aligned16(xp) && aligned16(g) && L <= 256) {
+        const int rows = std::min(SUM_ROWS, std::max(1, 256 / L));
+        const unsigned blocks = (unsigned)((t->N + rows - 1) / rows);
+        if (dtype == EIK_F32)
+            k_source_sum_vec<float, 4><<<blocks, rows * L, 0, st>>>(t->N, t->S, w, rows, t->cqn32, t->pos,
+                                                                    (const float *)xp, (long long)w, (float *)g, ld_g);
+        else
+            k_source_sum_vec<double, 2><<<blocks, rows * L, 0, st>>>(t->N, t->S, w, rows, t->cqn64, t->pos,
+                                                                     (const double *)xp, (long long)w, (double *)g, ld_g);
+    } else {
+        const long long n = t->N * w;
+        const unsigned blocks = (unsigned)((n + 255) / 256);
+        if (dtype == EIK_F32)
+            k_source_sum<float><<<blocks, 256, 0, st>>>(t->N, t->S, w, t->cqn32, t->pos, (const float *)xp, (long long)w,
+                                                        (float *)g, ld_g);
+        else
+            k_source_sum<double><<<blocks, 256, 0, st>>>(t->N, t->S, w, t->cqn64, t->pos, (const double *)xp, (long long)w,
+                                                         (double *)g, ld_g);
+    }
+    EIK_CHECK_LAUNCH();
+    return EIK_OK;
+}
+
 int traverse(Tangent *t, bool TR, int mode, const void *in, int shared_in, int R, void *out_full, void *out_aux,
              int sum_sources, int dtype, cudaStream_t st)
 {
@@ -1140,28 +1170,8 @@ int traverse(Tangent *t, bool TR, int mode, const void *in, int shared_in, int R
         else rc = TR ? dispatch_v<double, true>(t, P, st) : dispatch_v<double, false>(t, P, st);
         if (rc) return rc;
         if (TR && mode == MODE_J && sum_sources && out_aux) {
-            const int V = dtype == EIK_F32 ? 4 : 2;
-            const int L = w / V;
-            if (w % V == 0 && R % V == 0 && r0 % V == 0 && aligned16(xp) && aligned16(auxp) && L <= 256) {
-                const int rows = std::min(SUM_ROWS, std::max(1, 256 / L));
-                const unsigned blocks = (unsigned)((t->N + rows - 1) / rows);
-                if (dtype == EIK_F32)
-                    k_source_sum_vec<float, 4><<<blocks, rows * L, 0, st>>>(t->N, t->S, w, rows, t->cqn32, t->pos,
-                                                                            (const float *)xp, P.ld_x, (float *)auxp, (long long)R);
-                else
-                    k_source_sum_vec<double, 2><<<blocks, rows * L, 0, st>>>(t->N, t->S, w, rows, t->cqn64, t->pos,
-                                                                             (const double *)xp, P.ld_x, (double *)auxp, (long long)R);
-            } else {
-                long long n = t->N * w;
-                unsigned blocks = (unsigned)((n + 255) / 256);
-                if (dtype == EIK_F32)
-                    k_source_sum<float><<<blocks, 256, 0, st>>>(t->N, t->S, w, t->cqn32, t->pos, (const float *)xp, P.ld_x,
-                                                                (float *)auxp, (long long)R);
-                else
-                    k_source_sum<double><<<blocks, 256, 0, st>>>(t->N, t->S, w, t->cqn64, t->pos, (const double *)xp, P.ld_x,
-                                                                 (double *)auxp, (long long)R);
-            }
-            EIK_CHECK_LAUNCH();
+            rc = source_sum(t, w, auxp, (long long)R, dtype, st);
+            if (rc) return rc;
         }
     }
     return EIK_OK;

@@ -124,6 +124,16 @@ struct Tangent {
     int *done = nullptr;          // [S][maxL] completed items per (source, step)
     int *ticket = nullptr;        // [2]
     int *err = nullptr;           // [4] device fault latch {code, source, step, item}
+    // off-grid receivers (multilinear sampling), set by tangent_set_receivers
+    int n_ip = 0, ip_k = 0;       // receivers per source, corners per receiver (2^ndim)
+    int *ip_node = nullptr;       // [S][n_ip][ip_k] natural node of each corner
+    double *ip_w = nullptr;       // [S][n_ip][ip_k] multilinear weight
+    int n_ipt = 0;                // touched nodes per source (padded to the largest source)
+    int *ipt_node = nullptr;      // [S][n_ipt] touched nodes, ascending, -1 = padding
+    int *ipt_ptr = nullptr;       // [S][n_ipt+1] ranges into ipt_e
+    int *ipt_e = nullptr;         // [S][n_ip*ip_k] corner entries (receiver * ip_k + corner)
+    void *ws_in = nullptr;        // dense input / column-chunk staging of the interpolated paths
+    size_t ws_in_bytes = 0;
     // workspaces
     void *ws_vec = nullptr;       // internal dT / lam
     size_t ws_vec_bytes = 0;
@@ -153,6 +163,13 @@ int sweep(Tangent *t, bool transpose, const void *b, int R, void *x, int dtype,
           const eik_opts *opts, int *cycles, cudaStream_t stream);
 
 int ensure_workspace(Tangent *t, size_t vec_bytes, size_t blk_elems);
+// g (row stride ld_g) = sum over sources of c_a x_a for the w columns in the workspace
+int source_sum(Tangent *t, int w, void *g, long long ld_g, int dtype, cudaStream_t st);
+// off-grid receivers (multilinear P): set from host [S][n_rec][ndim] fractional indices,
+// then J p -> [S][n_rec][R] and J^T y -> [N][R] (summed over sources)
+int set_receivers_interp(Tangent *t, int n_rec, const double *f);
+int apply_interp_entry(Tangent *t, const void *ds, int shared, int R, void *d_rec, int dtype, cudaStream_t st);
+int apply_interp_T_entry(Tangent *t, const void *y, int R, void *g, int dtype, cudaStream_t st);
 
 void launch_sample(long long N, int S, int n_rec, const int *rec, const double *field, double *out, cudaStream_t st);
 

@@ -817,7 +817,8 @@ void free_tangent(Tangent *t)
                     t->rec_nat, t->nrow_cnt, t->nrow_node, t->nrow_w, t->cs_nat, t->blk_desc, t->blk_off, t->lu,
                     t->binv, t->piv, t->items_fwd, t->items_bwd, t->ebeg_fwd, t->ebeg_bwd, t->deps_fwd, t->deps_bwd,
                     t->ndeps_fwd, t->ndeps_bwd, t->item_done, t->item_cnt, t->done, t->ticket, t->err, t->ws_vec,
-                    t->ws_blk, t->ebase_d, t->tbase_d};
+                    t->ws_blk, t->ebase_d, t->tbase_d, t->ip_node, t->ip_w, t->ipt_node, t->ipt_ptr, t->ipt_e,
+                    t->ws_in};
     for (void *p : ptrs) if (p) cudaFree(p);
     if (t->params_d) cudaFree((void *)t->params_d);
     for (auto &kv : t->level_graphs) if (kv.second) cudaGraphExecDestroy(kv.second);

@@ -27,7 +27,8 @@ EXPORTED = ["eik_opts_default", "eik_last_error", "eik_version", "eik_forward", 
             "lsqr_create", "lsqr_start", "lsqr_iterate", "lsqr_solution", "lsqr_free",
             "eik_forward_noalloc", "eik_forward_noalloc_capacity",
             "gn_create", "gn_dims", "gn_apply", "gn_apply_T", "gn_lsmr_start", "gn_lsmr_iterate",
-            "gn_lsmr_solution", "gn_free", "model_cells_to_nodes", "model_nodes_to_cells"]
+            "gn_lsmr_solution", "gn_free", "model_cells_to_nodes", "model_nodes_to_cells",
+            "tangent_set_receivers", "tangent_apply_interp", "tangent_apply_interp_T"]
 
 
 class EikError(RuntimeError):
@@ -103,6 +104,9 @@ def lib():
         L.gn_free.argtypes = [P]
         L.gn_free.restype = None
         L.model_cells_to_nodes.argtypes = [C.POINTER(Grid_), P, I, P, I, P]
+        L.tangent_set_receivers.argtypes = [P, I, P]
+        L.tangent_apply_interp.argtypes = [P, P, I, I, P, I, P]
+        L.tangent_apply_interp_T.argtypes = [P, P, I, P, I, P]
         L.model_nodes_to_cells.argtypes = [C.POINTER(Grid_), P, I, P, I, P]
         L.sweep_apply.argtypes = [P, I, P, I, P, I, C.POINTER(Opts), C.POINTER(I), P]
         _lib = L
@@ -264,6 +268,30 @@ class Tangent:
                                      _dev(lam_full, y.dtype, "lam_full") if lam_full is not None else None,
                                      _dt(y.dtype), _stream()))
         return g, lam_full
+
+    def set_receivers(self, f):
+        """Off-grid receivers: f [S, n_rec, ndim] fractional logical indices (host array)."""
+        import numpy as np
+        f = np.ascontiguousarray(np.asarray(f, dtype=np.float64))
+        assert f.ndim == 3 and f.shape[0] == self.S
+        self.n_ip = int(f.shape[1])
+        _check(lib().tangent_set_receivers(self.h, self.n_ip, C.c_void_p(f.ctypes.data)))
+
+    def apply_interp(self, p: torch.Tensor, shared_model: bool = True):
+        """J p sampled at the off-grid receivers: returns [S, n_rec, R]."""
+        R = p.shape[-1]
+        out = torch.empty((self.S, self.n_ip, R), dtype=p.dtype, device=p.device)
+        _check(lib().tangent_apply_interp(self.h, _dev(p, name="p"), int(shared_model), R, _dev(out, p.dtype, "d_rec"),
+                                          _dt(p.dtype), _stream()))
+        return out
+
+    def apply_interp_T(self, y: torch.Tensor):
+        """J^T y for data at the off-grid receivers y [S, n_rec, R]: returns [N, R]."""
+        R = y.shape[-1]
+        g = torch.empty((self.N, R), dtype=y.dtype, device=y.device)
+        _check(lib().tangent_apply_interp_T(self.h, _dev(y, name="y"), R, _dev(g, y.dtype, "g"), _dt(y.dtype),
+                                            _stream()))
+        return g
 
     def solve(self, q: torch.Tensor, out=None):
         """A^-1 q for every source: q [S, N, R]."""
