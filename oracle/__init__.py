@@ -422,24 +422,35 @@ def roughness(grid):
     return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(r0, N))
 
 
-def gn_operator(grid, tans, s, rec, wd, vk, lam, gamma, model=MODEL_VELOCITY):
+def gn_operator(grid, tans, s, rec, wd, vk, lam, gamma, model=MODEL_VELOCITY, cells=False):
     """The augmented Gauss-Newton operator of Eq. (augmented-actions):
         K p   = [W_d J p ; lam R p ; lam S p],        S = gamma diag(1 / v_k)  (Eq. relative-damping)
         K^T y = J^T W_d y_d + lam R^T y_R + lam S^T y_S.
-    wd: [S, n_rec] diagonal of W_d; vk: [N] current model.  p is [N]; y is
-    [S*n_rec + n_rough + N].  Returns (apply_K, apply_KT, n_rows)."""
-    Rm = roughness(grid)
+    wd: [S, n_rec] diagonal of W_d; vk: the current model.  With cells=True the model
+    lives on the cells (cell_average): J acts through A (J A p, A^T J^T y), R takes first
+    differences on the cell grid and vk is [n_cells].  p is the model vector; y is
+    [S*n_rec + n_rough + n_model].  Returns (apply_K, apply_KT, n_rows)."""
+    if cells:
+        A = cell_average(grid)
+        cgrid = type("CellGrid", (), {"ndim": grid.ndim, "n": tuple(m - 1 for m in grid.n[:grid.ndim])})()
+        Rm = roughness(cgrid)
+    else:
+        A = None
+        Rm = roughness(grid)
     S_, nr = len(tans), len(rec)
     nd, nR, N = S_ * nr, Rm.shape[0], len(vk)
     sdiag = gamma / np.asarray(vk, dtype=np.float64)
 
     def apply_K(p):
-        d = J(tans, s, rec, p[:, None], model=model)[:, :, 0] * wd
+        pn = A @ p if cells else p
+        d = J(tans, s, rec, pn[:, None], model=model)[:, :, 0] * wd
         return np.concatenate([d.ravel(), lam * (Rm @ p), lam * sdiag * p])
 
     def apply_KT(y):
         yd = (y[:nd].reshape(S_, nr) * wd)[:, :, None]
         g = JT(tans, s, rec, yd, model=model)[:, 0]
+        if cells:
+            g = A.T @ g
         return g + lam * (Rm.T @ y[nd:nd + nR]) + lam * sdiag * y[nd + nR:]
 
     return apply_K, apply_KT, nd + nR + N

@@ -102,3 +102,30 @@ def test_gn_operator_adjoint_and_normal_equations(oracle_mod):
     dv, info = O.lsmr(K, KT, b, 400)
     assert np.max(np.abs(dv - dv_ne)) <= 1e-7 * np.max(np.abs(dv_ne))
     assert info["normar"] <= 1e-9 * info["norma"] * info["normr"]
+
+
+def test_gn_operator_on_cells_normal_equations(oracle_mod):
+    """The same minimizer check with the model on cells: LSMR on K_cells reaches the
+    solution of (A^T J^T W_d^2 J A + lam^2 R_c^T R_c + lam^2 S_c^2) dv = -A^T J^T W_d^2 r."""
+    O = oracle_mod
+    g, tans, s, rec = _gn_case(O)
+    rng = np.random.default_rng(8)
+    A = O.cell_average(g)
+    nc = A.shape[1]
+    vc = 2.0 + rng.uniform(0.0, 0.5, nc)
+    wd = 1.0 / (0.0003 + 0.003 * rng.uniform(0.5, 1.5, (len(tans), len(rec))))
+    lam, gamma = 0.5, 1.0
+    K, KT, m = O.gn_operator(g, tans, s, rec, wd, vc, lam, gamma, cells=True)
+    p, y = rng.standard_normal(nc), rng.standard_normal(m)
+    l1, l2 = float(K(p) @ y), float(p @ KT(y))
+    assert abs(l1 - l2) <= 1e-12 * max(abs(l1), abs(l2))
+    Jd = O.J(tans, s, rec, np.asarray(A.todense()), model=O.MODEL_VELOCITY).reshape(len(tans) * len(rec), nc)
+    cg = W.Grid(3, tuple(x - 1 for x in g.n), g.dxi, np.zeros((nc, 3)))
+    Rc = O.roughness(cg).toarray()
+    Wd = wd.ravel()
+    r = rng.standard_normal(Wd.size) * 1e-3
+    H = Jd.T @ (Wd[:, None] ** 2 * Jd) + lam ** 2 * (Rc.T @ Rc) + lam ** 2 * np.diag((gamma / vc) ** 2)
+    dv_ne = np.linalg.solve(H, -Jd.T @ (Wd ** 2 * r))
+    b = np.concatenate([-Wd * r, np.zeros(m - Wd.size)])
+    dv, info = O.lsmr(K, KT, b, 400)
+    assert np.max(np.abs(dv - dv_ne)) <= 1e-7 * np.max(np.abs(dv_ne))
