@@ -384,6 +384,13 @@ int model_nodes_to_cells(const eik_grid *g, const void *g_node, int R, void *g_c
 typedef struct eik_gn eik_gn;
 int gn_create(eik_tangent *t, const double *wd, const double *vk, double lambda, double gamma, int dtype,
               eik_gn **out);
+/* The same operator with the model on the cells (one per grid hexahedron, see
+ * model_cells_to_nodes): K p = [W_d J A p; lambda R_c p; lambda S p], with A the node <-
+ * cell map, R_c first differences on the cell grid (extents n_d - 1) and S = gamma
+ * diag(1 / v_cells); v_cells device FP64 [n_cells].  Model vectors (p, K^T y, the LSMR
+ * solution) are [n_cells]. */
+int gn_create_cells(eik_tangent *t, const double *wd, const double *v_cells, double lambda, double gamma, int dtype,
+                    eik_gn **out);
 int gn_dims(const eik_gn *g, int64_t *n_rows, int64_t *n_data, int64_t *n_rough);
 int gn_apply(eik_gn *g, const void *p, void *out, eik_stream stream);
 int gn_apply_T(eik_gn *g, const void *y, void *out, eik_stream stream);

@@ -18,17 +18,17 @@ struct CellGrid {
     long long cst[3];    // cell strides (extents n_d - 1)
 };
 
-static CellGrid make_cells(const eik_grid *g)
+static CellGrid make_cells(int ndim, const int *n)
 {
     CellGrid c{};
-    c.nd = g->ndim;
+    c.nd = ndim;
     long long sn = 1, sc = 1;
-    for (int d = g->ndim - 1; d >= 0; --d) {
-        c.n[d] = g->n[d];
+    for (int d = ndim - 1; d >= 0; --d) {
+        c.n[d] = n[d];
         c.nst[d] = sn;
         c.cst[d] = sc;
-        sn *= g->n[d];
-        sc *= g->n[d] - 1;
+        sn *= n[d];
+        sc *= n[d] - 1;
     }
     return c;
 }
@@ -88,17 +88,23 @@ __global__ void k_nodes_to_cells(CellGrid C, long long NC, int R, const T *__res
 }
 
 template <typename T>
-static int cells_map(const eik_grid *g, const void *in, int R, void *out, bool to_nodes, cudaStream_t st)
+static int cells_map(int ndim, const int *n, const void *in, int R, void *out, bool to_nodes, cudaStream_t st)
 {
-    const CellGrid C = make_cells(g);
+    const CellGrid C = make_cells(ndim, n);
     long long N = 1, NC = 1;
-    for (int d = 0; d < g->ndim; ++d) { N *= g->n[d]; NC *= g->n[d] - 1; }
+    for (int d = 0; d < ndim; ++d) { N *= n[d]; NC *= n[d] - 1; }
     const long long work = (to_nodes ? N : NC) * R;
     const unsigned blocks = (unsigned)((work + 255) / 256);
     if (to_nodes) k_cells_to_nodes<T><<<blocks, 256, 0, st>>>(C, N, R, (const T *)in, (T *)out);
     else k_nodes_to_cells<T><<<blocks, 256, 0, st>>>(C, NC, R, (const T *)in, (T *)out);
     EIK_CHECK_LAUNCH();
     return EIK_OK;
+}
+
+int cell_map(int ndim, const int *n, const void *in, int R, void *out, bool to_nodes, int dtype, cudaStream_t st)
+{
+    return dtype == EIK_F32 ? cells_map<float>(ndim, n, in, R, out, to_nodes, st)
+                            : cells_map<double>(ndim, n, in, R, out, to_nodes, st);
 }
 
 static int cells_entry(const eik_grid *g, const void *in, int R, void *out, int dtype, bool to_nodes,
@@ -110,8 +116,7 @@ static int cells_entry(const eik_grid *g, const void *in, int R, void *out, int 
     }
     for (int d = 0; d < g->ndim; ++d)
         if (g->n[d] < 2) { set_error("grid needs >= 2 nodes per axis"); return EIK_ERR_INVALID; }
-    cudaStream_t st = (cudaStream_t)stream;
-    return dtype == EIK_F32 ? cells_map<float>(g, in, R, out, to_nodes, st) : cells_map<double>(g, in, R, out, to_nodes, st);
+    return cell_map(g->ndim, g->n, in, R, out, to_nodes, dtype, (cudaStream_t)stream);
 }
 
 }  // namespace eik

@@ -286,7 +286,9 @@ struct eik_tangent { Tangent *impl; };
 struct eik_gn {
     eik_tangent *t = nullptr;
     int dtype = EIK_F64;
-    long long N = 0, nd = 0, nR = 0, n_rows = 0;
+    int cells = 0;                 // model on the cells (one per grid hexahedron), not the nodes
+    long long N = 0, nd = 0, nR = 0, n_rows = 0;   // N: model size (nodes or cells)
+    void *pn = nullptr, *gc = nullptr;             // cells: node-space input of J, cell-space J^T
     RoughGrid R{};
     double lam = 0.0, gamma = 0.0;
     double *wd = nullptr, *sdiag = nullptr;                 // device copies of W_d and gamma / v_k
@@ -311,7 +313,14 @@ int nblocks(long long n)
 template <typename T>
 int gn_forward(eik_gn *G, const void *p, void *out, int coef_slot, double *partial, cudaStream_t st)
 {
-    int rc = traverse(G->t->impl, false, MODE_J, p, 1, 1, nullptr, G->jp, 0, G->dtype, st);
+    const void *pj = p;
+    if (G->cells) {   // J acts on the nodal perturbation A p
+        const GridDesc &gd = G->t->impl->grid;
+        int rc = cell_map(gd.ndim, gd.n, p, 1, G->pn, true, G->dtype, st);
+        if (rc) return rc;
+        pj = G->pn;
+    }
+    int rc = traverse(G->t->impl, false, MODE_J, pj, 1, 1, nullptr, G->jp, 0, G->dtype, st);
     if (rc) return rc;
     k_gn_forward<T><<<G->nb_rows, LB, 0, st>>>(G->nd, G->N, G->R, G->lam, G->wd, G->sdiag, (const T *)G->jp,
                                                (const T *)p, (T *)out, G->sc, coef_slot, partial);
@@ -327,7 +336,14 @@ int gn_transpose(eik_gn *G, const void *y, void *out, int coef_slot, double *par
     EIK_CHECK_LAUNCH();
     int rc = traverse(G->t->impl, true, MODE_J, G->yw, 0, 1, nullptr, G->g, 1, G->dtype, st);
     if (rc) return rc;
-    k_gn_transpose<T><<<G->nb_model, LB, 0, st>>>(G->nd, G->N, G->R, G->lam, G->sdiag, (const T *)G->g,
+    const void *gm = G->g;
+    if (G->cells) {   // A^T (J^T W_d y_d)
+        const GridDesc &gd = G->t->impl->grid;
+        rc = cell_map(gd.ndim, gd.n, G->g, 1, G->gc, false, G->dtype, st);
+        if (rc) return rc;
+        gm = G->gc;
+    }
+    k_gn_transpose<T><<<G->nb_model, LB, 0, st>>>(G->nd, G->N, G->R, G->lam, G->sdiag, (const T *)gm,
                                                   (const T *)y, (T *)out, G->sc, coef_slot, partial);
     EIK_CHECK_LAUNCH();
     return EIK_OK;
@@ -387,12 +403,14 @@ void gn_free(eik_gn *G)
     cudaDeviceSynchronize();
     if (G->exec) cudaGraphExecDestroy(G->exec);
     if (G->graph) cudaGraphDestroy(G->graph);
-    void *ptrs[] = {G->wd, G->sdiag, G->u, G->v, G->h, G->hbar, G->x, G->jp, G->yw, G->g, G->sc, G->partial};
+    void *ptrs[] = {G->wd, G->sdiag, G->u, G->v, G->h, G->hbar, G->x, G->jp, G->yw, G->g, G->sc, G->partial,
+                    G->pn, G->gc};
     for (void *p : ptrs) if (p) cudaFree(p);
     delete G;
 }
 
-int gn_create(eik_tangent *t, const double *wd, const double *vk, double lambda, double gamma, int dtype, eik_gn **out)
+static int gn_make(eik_tangent *t, const double *wd, const double *vk, double lambda, double gamma, int dtype,
+                   int cells, eik_gn **out)
 {
     try {
         if (!out) { set_error("out is NULL"); return EIK_ERR_INVALID; }
@@ -406,9 +424,16 @@ int gn_create(eik_tangent *t, const double *wd, const double *vk, double lambda,
         eik_gn *G = new eik_gn();
         G->t = t;
         G->dtype = dtype;
-        G->N = T->N;
+        G->cells = cells;
+        GridDesc mg = T->grid;       // the grid R differences on: nodes, or cells (extents n_d - 1)
+        if (cells) {
+            long long nc = 1;
+            for (int d = 0; d < mg.ndim; ++d) { mg.n[d] -= 1; nc *= mg.n[d]; }
+            mg.N = nc;
+        }
+        G->N = cells ? mg.N : T->N;
         G->nd = (long long)T->S * T->n_rec;
-        G->R = make_rough(T->grid);
+        G->R = make_rough(mg);
         G->nR = G->R.r0[G->R.nd];
         G->n_rows = G->nd + G->nR + G->N;
         G->lam = lambda;
@@ -418,8 +443,11 @@ int gn_create(eik_tangent *t, const double *wd, const double *vk, double lambda,
         const size_t es = dtype == EIK_F32 ? 4 : 8;
         cudaError_t e = cudaMalloc((void **)&G->wd, G->nd * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc((void **)&G->sdiag, G->N * sizeof(double));
-        void **model[] = {&G->v, &G->h, &G->hbar, &G->x, &G->g};
+        void **model[] = {&G->v, &G->h, &G->hbar, &G->x};
         for (void **p : model) if (e == cudaSuccess) e = cudaMalloc(p, G->N * es);
+        if (e == cudaSuccess) e = cudaMalloc(&G->g, T->N * es);
+        if (cells && e == cudaSuccess) e = cudaMalloc(&G->pn, T->N * es);
+        if (cells && e == cudaSuccess) e = cudaMalloc(&G->gc, G->N * es);
         if (e == cudaSuccess) e = cudaMalloc(&G->u, G->n_rows * es);
         if (e == cudaSuccess) e = cudaMalloc(&G->jp, G->nd * es);
         if (e == cudaSuccess) e = cudaMalloc(&G->yw, G->nd * es);
@@ -443,6 +471,17 @@ int gn_create(eik_tangent *t, const double *wd, const double *vk, double lambda,
         set_error("gn_create failed");
         return EIK_ERR_OOM;
     }
+}
+
+int gn_create(eik_tangent *t, const double *wd, const double *vk, double lambda, double gamma, int dtype, eik_gn **out)
+{
+    return gn_make(t, wd, vk, lambda, gamma, dtype, 0, out);
+}
+
+int gn_create_cells(eik_tangent *t, const double *wd, const double *v_cells, double lambda, double gamma, int dtype,
+                    eik_gn **out)
+{
+    return gn_make(t, wd, v_cells, lambda, gamma, dtype, 1, out);
 }
 
 int gn_dims(const eik_gn *G, int64_t *n_rows, int64_t *n_data, int64_t *n_rough)

@@ -167,6 +167,8 @@ int ensure_workspace(Tangent *t, size_t vec_bytes, size_t blk_elems);
 int source_sum(Tangent *t, int w, void *g, long long ld_g, int dtype, cudaStream_t st);
 // off-grid receivers (multilinear P): set from host [S][n_rec][ndim] fractional indices,
 // then J p -> [S][n_rec][R] and J^T y -> [N][R] (summed over sources)
+// node <- cell averaging map (to_nodes) or its transpose, vectors [.][R]
+int cell_map(int ndim, const int *n, const void *in, int R, void *out, bool to_nodes, int dtype, cudaStream_t st);
 int set_receivers_interp(Tangent *t, int n_rec, const double *f);
 int apply_interp_entry(Tangent *t, const void *ds, int shared, int R, void *d_rec, int dtype, cudaStream_t st);
 int apply_interp_T_entry(Tangent *t, const void *y, int R, void *g, int dtype, cudaStream_t st);

@@ -28,7 +28,7 @@ EXPORTED = ["eik_opts_default", "eik_last_error", "eik_version", "eik_forward", 
             "eik_forward_noalloc", "eik_forward_noalloc_capacity",
             "gn_create", "gn_dims", "gn_apply", "gn_apply_T", "gn_lsmr_start", "gn_lsmr_iterate",
             "gn_lsmr_solution", "gn_free", "model_cells_to_nodes", "model_nodes_to_cells",
-            "tangent_set_receivers", "tangent_apply_interp", "tangent_apply_interp_T"]
+            "tangent_set_receivers", "tangent_apply_interp", "tangent_apply_interp_T", "gn_create_cells"]
 
 
 class EikError(RuntimeError):
@@ -95,6 +95,7 @@ def lib():
         L.lsqr_free.argtypes = [P]
         L.lsqr_free.restype = None
         L.gn_create.argtypes = [P, P, P, D, D, I, C.POINTER(P)]
+        L.gn_create_cells.argtypes = [P, P, P, D, D, I, C.POINTER(P)]
         L.gn_dims.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.gn_apply.argtypes = [P, P, P, P]
         L.gn_apply_T.argtypes = [P, P, P, P]
@@ -398,12 +399,14 @@ class GN:
     W_d); vk: [N] FP64 current model (S_k = gamma diag(1 / vk))."""
 
     def __init__(self, tan: Tangent, wd: torch.Tensor, vk: torch.Tensor, lam: float, gamma: float,
-                 dtype=torch.float64):
+                 dtype=torch.float64, cells: bool = False):
         self.tan = tan
         self.dtype = dtype
+        self.n_model = int(vk.numel())    # nodes, or cells when cells=True
         h = C.c_void_p()
-        _check(lib().gn_create(tan.h, _dev(wd, torch.float64, "wd"), _dev(vk, torch.float64, "vk"), float(lam),
-                               float(gamma), _dt(dtype), C.byref(h)))
+        create = lib().gn_create_cells if cells else lib().gn_create
+        _check(create(tan.h, _dev(wd, torch.float64, "wd"), _dev(vk, torch.float64, "vk"), float(lam),
+                      float(gamma), _dt(dtype), C.byref(h)))
         self.h = h
         a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
         _check(lib().gn_dims(self.h, C.byref(a), C.byref(b), C.byref(c)))
@@ -423,7 +426,7 @@ class GN:
         return out
 
     def apply_T(self, y: torch.Tensor) -> torch.Tensor:
-        out = torch.empty(self.tan.N, dtype=self.dtype, device="cuda")
+        out = torch.empty(self.n_model, dtype=self.dtype, device="cuda")
         _check(lib().gn_apply_T(self.h, _dev(y, self.dtype, "y"), _dev(out, self.dtype, "out"), _stream()))
         return out
 
@@ -440,7 +443,7 @@ class GN:
         _check(lib().gn_lsmr_iterate(self.h, iters, int(use_graph), _stream()))
 
     def solution(self):
-        x = torch.empty(self.tan.N, dtype=self.dtype, device="cuda")
+        x = torch.empty(self.n_model, dtype=self.dtype, device="cuda")
         sc = (C.c_double * 6)()
         _check(lib().gn_lsmr_solution(self.h, _dev(x, self.dtype, "x"), sc, _stream()))
         names = ("normr", "normar", "norma", "normx", "normb", "iters")

@@ -130,3 +130,37 @@ def test_gn_lsmr_fp32_and_stopping_rule(oracle_mod):
     _, info = oracle_mod.lsmr(K, KT, b, 400)
     rx = np.linalg.norm(b - K(x.double().cpu().numpy()))
     assert abs(rx - info["normr"]) <= 1e-3 * info["normr"]
+
+
+@pytest.mark.parametrize("case", [_case_2d, _case_3d])
+def test_gn_on_cells_against_oracle(oracle_mod, case):
+    """The operator with the model on cells (J A p, R on the cell grid, S on cell
+    velocities): K p, K^T y and 5 LSMR iterations against the oracle (FP64)."""
+    g, Ts, s, srcs, rec, lam = case()
+    _, G, _ = oracle_mod.metric(g)
+    otans = [oracle_mod.build_tangent(g, G, Ts[a], s, int(srcs[a])) for a in range(len(srcs))]
+    tan = eik.Tangent(eik.DeviceGrid(g), torch.tensor(Ts, device=DEV), torch.tensor(s, device=DEV), srcs, rec=rec,
+                      opts=eik.default_opts(model=eik.MODEL_VELOCITY))
+    rng = np.random.default_rng(41)
+    nc = oracle_mod.cell_average(g).shape[1]
+    vc = 2.0 + rng.uniform(0.0, 0.5, nc)
+    wd = 1.0 / (3e-4 + 3e-3 * rng.uniform(0.5, 1.5, (len(srcs), len(rec))))
+    K, KT, m = oracle_mod.gn_operator(g, otans, s, rec, wd, vc, lam, 1.0, cells=True)
+    gn = eik.GN(tan, torch.tensor(wd, device=DEV), torch.tensor(vc, device=DEV), lam, 1.0, cells=True)
+    assert gn.n_rows == m and gn.n_model == nc
+    p = torch.tensor(rng.standard_normal(nc), device=DEV)
+    y = torch.tensor(rng.standard_normal(m), device=DEV)
+    Kp, KTy = gn.apply(p), gn.apply_T(y)
+    tan.status()
+    assert _rel(Kp, K(p.cpu().numpy())) <= 1e-10
+    assert _rel(KTy, KT(y.cpu().numpy())) <= 1e-10
+    b = np.concatenate([-(wd * rng.standard_normal(wd.shape) * 1e-3).ravel(), np.zeros(m - wd.size)])
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        gn.start(torch.tensor(b, device=DEV))
+        gn.iterate(5, use_graph=True)
+        x5, sc5 = gn.solution()
+    stream.synchronize()
+    xo, info = oracle_mod.lsmr(K, KT, b, 5)
+    assert _rel(x5, xo) <= 1e-9
+    assert abs(sc5["normr"] - info["normr"]) <= 1e-9 * info["normr"]
