@@ -427,9 +427,17 @@ def run_gn(args):
     gen = torch.Generator("cuda").manual_seed(20265)
     r = sigma * torch.randn(d.shape, device="cuda", dtype=torch.float64, generator=gen)
     dtype = torch.float64 if args.lsqr_dtype == "f64" else torch.float32
+    if args.cells:
+        # cell velocities: the mean of each hexahedron's corner-node velocities
+        v = (1.0 / s).reshape(g.n)
+        vc = sum(v[i:i + g.n[0] - 1, j:j + g.n[1] - 1, k:k + g.n[2] - 1]
+                 for i in (0, 1) for j in (0, 1) for k in (0, 1)) / 8.0
+        vmodel = vc.contiguous().reshape(-1)
+    else:
+        vmodel = (1.0 / s).contiguous()
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        gn = eik.GN(tan, wd, (1.0 / s).contiguous(), 0.01, 0.1, dtype=dtype)
+        gn = eik.GN(tan, wd, vmodel, 0.01, 0.1, dtype=dtype, cells=args.cells)
         b = gn.rhs(r, wd)
         gn.start(b)
         gn.iterate(1, use_graph=True)           # capture + first replay
@@ -446,7 +454,8 @@ def run_gn(args):
     upd = 2.0 * N * S
     out = {"metric": METRIC, "value": upd / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": 20, "warmup": 1,
            "ms_per_step": ms, "higher_is_better": True, "dtype": args.lsqr_dtype,
-           "config": {"workload": f"3d-201x201x101-S{S}-lsmr (Gauss-Newton inner solve, Sec. 4.5)", "nodes": N,
+           "config": {"workload": f"3d-201x201x101-S{S}-lsmr{'-cells' if args.cells else ''} (Gauss-Newton inner solve, Sec. 4.5)",
+                      "nodes": N, "model": "cells" if args.cells else "nodes", "model_size": gn.n_model,
                       "sources": S, "receivers": len(wl.rec), "rows": gn.n_rows, "lambda": 0.01, "gamma": 0.1,
                       "step": "one LSMR iteration on K (J v, J^T u, W_d / R / S_k epilogues), CUDA graph"},
            "lsmr": {"iterations_to_atol_1e-4": int(sc["iters"]), "normr": sc["normr"], "normar": sc["normar"],
@@ -642,6 +651,7 @@ def main():
     ap.add_argument("--sources", type=int, default=0, help="use only the first K sources (small profiling case)")
     ap.add_argument("--state-cache", default="", help="load/save the solved states (.npy) to skip the state solve")
     ap.add_argument("--gn-max-iters", type=int, default=300)
+    ap.add_argument("--cells", action="store_true", help="gn workload: the model on the grid cells")
     ap.add_argument("--workload", choices=["apply", "lsqr", "gn", "stress", "state"], default="apply",
                     help="apply: the benchmark line (3-D apply config); lsqr: the 20-iteration Krylov config; "
                          "gn: LSMR on the augmented Gauss-Newton operator (Sec. 4.5); "
