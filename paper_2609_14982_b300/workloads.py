@@ -12,7 +12,7 @@ Conventions
 * Physical coordinates: x (and y) equal the horizontal logical coordinates; z is
   depth, positive downwards, z = zeta + (1 - zeta/H) * zsurf(x, y) (the map of
   Sec. 5.1, Eq. (test-map), and Sec. 5.2, Eq. (graph-map)), where zsurf is the
-  depth of the top surface.  For the BASELINE workloads the topography is given as
+  depth of the top surface.  For the benchmark workloads the topography is given as
   an elevation e (positive up), so zsurf = -e and "depth" in a velocity law is z
   measured from the datum z = 0.
 """
