@@ -253,16 +253,20 @@ long or_scc(long N, const long *row_ptr, const int *col, int *label)
 /* comp_ptr[ncomp+1] (component boundaries in perm), level_ptr[nlev+1].       */
 /* Returns the number of levels, or -1 if the condensation is not acyclic.   */
 /* ------------------------------------------------------------------------ */
+/* canonical order key: (level, smallest node of the component, node), compared in that order */
+typedef struct { long lev, comp, node; } order_key;
+
 static int cmp_key(const void *a, const void *b)
 {
-    const long long *x = a, *y = b;
-    return (*x > *y) - (*x < *y);
+    const order_key *x = a, *y = b;
+    if (x->lev != y->lev) return (x->lev > y->lev) - (x->lev < y->lev);
+    if (x->comp != y->comp) return (x->comp > y->comp) - (x->comp < y->comp);
+    return (x->node > y->node) - (x->node < y->node);
 }
 
 long or_levels(long N, const long *row_ptr, const int *col, const int *label,
                int *level, int *perm, long *comp_ptr, long *level_ptr, long *ncomp_out)
 {
-    if (N >= (1L << 22)) return -2;   /* sort key packs node indices in 22 bits */
     /* compact component ids by smallest node */
     long *cid = malloc(N * sizeof(long));
     long m = 0;
@@ -303,16 +307,18 @@ long or_levels(long N, const long *row_ptr, const int *col, const int *label,
     long ok = (qt == m);
     if (ok) {
         /* sort nodes by (level, smallest node of component, node) */
-        long long *key = malloc(N * sizeof(long long));
+        order_key *key = malloc(N * sizeof(order_key));
         for (long v = 0; v < N; ++v) {
             level[v] = (int)clev[cid[v]];
-            key[v] = ((long long)clev[cid[v]] << 44) | ((long long)label[v] << 22) | (long long)v;
+            key[v].lev = clev[cid[v]];
+            key[v].comp = label[v];
+            key[v].node = v;
         }
-        qsort(key, N, sizeof(long long), cmp_key);
+        qsort(key, N, sizeof(order_key), cmp_key);
         long nc = 0;
         for (long p = 0; p <= nlev; ++p) level_ptr[p] = -1;
         for (long p = 0; p < N; ++p) {
-            int v = (int)(key[p] & ((1LL << 22) - 1));
+            int v = (int)key[p].node;
             perm[p] = v;
             if (p == 0 || label[perm[p - 1]] != label[v]) comp_ptr[nc++] = p;
             if (level_ptr[level[v]] < 0) level_ptr[level[v]] = p;
