@@ -404,9 +404,10 @@ __global__ void k_node_level(long long SN, long long N, const int *__restrict__ 
     atomicMax(&lmax[a], L);
 }
 
-// sort key: (source, level) segment | component id (local smallest node) | node
-__global__ void k_keys(long long SN, long long N, int maxL, const int *__restrict__ label, const int *__restrict__ level,
-                       unsigned long long *keys)
+// sort key: (source, level) segment | component id (local smallest node) | node, the last
+// two in nb bits each (nb = bits of N - 1), the segment above them
+__global__ void k_keys(long long SN, long long N, int maxL, int nb, const int *__restrict__ label,
+                       const int *__restrict__ level, unsigned long long *keys)
 {
     long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (v >= SN) return;
@@ -414,10 +415,10 @@ __global__ void k_keys(long long SN, long long N, int maxL, const int *__restric
     unsigned long long seg = (unsigned long long)(a * maxL + level[v]);
     unsigned long long comp = (unsigned long long)(label[v] - a * N);
     unsigned long long node = (unsigned long long)(v - a * N);
-    keys[v] = (seg << 44) | (comp << 22) | node;
+    keys[v] = (seg << (2 * nb)) | (comp << nb) | node;
 }
 
-__global__ void k_perm(long long SN, long long N, int maxL, const unsigned long long *__restrict__ skeys,
+__global__ void k_perm(long long SN, long long N, int maxL, int nb, const unsigned long long *__restrict__ skeys,
                        const int *__restrict__ label, const int *__restrict__ csize, int *perm, int *pos, int *lcount,
                        int *head)
 {
@@ -425,8 +426,9 @@ __global__ void k_perm(long long SN, long long N, int maxL, const unsigned long 
     if (p >= SN) return;
     unsigned long long key = skeys[p];
     long long a = p / N, pl = p - a * N;
-    int node = (int)(key & ((1ull << 22) - 1));
-    int seg = (int)(key >> 44);
+    const unsigned long long mask = (1ull << nb) - 1;
+    int node = (int)(key & mask);
+    int seg = (int)(key >> (2 * nb));
     long long v = a * N + node;
     bool member = csize[label[v]] > 1;
     perm[p] = member ? ~node : node;
@@ -436,7 +438,7 @@ __global__ void k_perm(long long SN, long long N, int maxL, const unsigned long 
     if (member) {
         if (pl == 0) is_head = 1;
         else {
-            int prev = (int)(skeys[p - 1] & ((1ull << 22) - 1));
+            int prev = (int)(skeys[p - 1] & mask);
             is_head = label[a * N + prev] != label[v];
         }
     }
@@ -833,7 +835,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
     GridDesc g = make_grid_desc(gin);
     const long long N = g.N, SN = N * (long long)S;
     const int nd = g.ndim, slots = 2 * nd;
-    if (N >= (1ll << 22)) { set_error("grid has %lld nodes; at most 2^22 - 1 supported", N); return EIK_ERR_INVALID; }
+    if (SN >= (1ll << 31)) { set_error("sources x nodes = %lld; at most 2^31 - 1 supported", SN); return EIK_ERR_INVALID; }
     for (int a = 0; a < S; ++a)
         if (src_node[a] < 0 || src_node[a] >= N) { set_error("source %d node %d out of range", a, src_node[a]); return EIK_ERR_INVALID; }
 
@@ -977,7 +979,13 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
     t->maxL = maxL;
     int segbits = 1;
     while ((1ll << segbits) < (long long)S * maxL) ++segbits;
-    if (segbits > 20) { set_error("too many (source, level) segments"); return fail(EIK_ERR_INVALID); }
+    int nb = 1;                  // bits of a local node index
+    while ((1ll << nb) < N) ++nb;
+    if (2 * nb + segbits > 64) {
+        set_error("%lld nodes and %lld (source, level) segments do not fit one 64-bit sort key; build fewer sources "
+                  "per tangent", N, (long long)S * maxL);
+        return fail(EIK_ERR_INVALID);
+    }
 
     // ---- canonical order: sort by (source, level, component, node)
     unsigned long long *keys, *skeys;
@@ -988,16 +996,16 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
     TRY(sc.get(&head, SN));
     TRY(dalloc(&t->perm, SN));
     TRY(dalloc(&t->pos, SN));
-    k_keys<<<blocks_for(SN), 256, 0, st>>>(SN, N, maxL, lab, t->level, keys);
+    k_keys<<<blocks_for(SN), 256, 0, st>>>(SN, N, maxL, nb, lab, t->level, keys);
     {
         size_t tb = 0;
-        TRY(cub::DeviceRadixSort::SortKeys(nullptr, tb, keys, skeys, (int64_t)SN, 0, 44 + segbits, st));
+        TRY(cub::DeviceRadixSort::SortKeys(nullptr, tb, keys, skeys, (int64_t)SN, 0, 2 * nb + segbits, st));
         void *tmp;
         TRY(sc.get((char **)&tmp, tb));
-        TRY(cub::DeviceRadixSort::SortKeys(tmp, tb, keys, skeys, (int64_t)SN, 0, 44 + segbits, st));
+        TRY(cub::DeviceRadixSort::SortKeys(tmp, tb, keys, skeys, (int64_t)SN, 0, 2 * nb + segbits, st));
     }
     TRY(cudaMemsetAsync(lcount, 0, (size_t)S * maxL * sizeof(int), st));
-    k_perm<<<blocks_for(SN), 256, 0, st>>>(SN, N, maxL, skeys, lab, csize, t->perm, t->pos, lcount, head);
+    k_perm<<<blocks_for(SN), 256, 0, st>>>(SN, N, maxL, nb, skeys, lab, csize, t->perm, t->pos, lcount, head);
     TRY(cudaGetLastError());
     std::vector<int> hl((size_t)S * maxL);
     TRY(cudaMemcpyAsync(hl.data(), lcount, hl.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
