@@ -569,6 +569,59 @@ def run_state(args):
     print(json.dumps(out), flush=True)
 
 
+def run_tables(args):
+    """The paper's structure-stress grids (Sec. 5.2.2, Table 3 refinement of case C: the
+    curved-surface map with A = 500 m, eps_T = 0.05, quarter source), one source each:
+    tangent_build time, SCC statistics, and J p + J^T y node-updates/s at R = 64 (FP32)."""
+    import torch
+
+    from paper_2609_14982_b300 import eik
+    from paper_2609_14982_b300 import workloads as W
+    torch.cuda.set_device(0)
+    rows, tot_upd, tot_ms = [], 0.0, 0.0
+    for n in ((21, 21, 13), (41, 41, 25), (61, 61, 37), (81, 81, 49)):
+        g = W.graph_grid(n, 500.0)
+        src = W.quarter_source(g)
+        st = W.curved_state(g, src, 0.05)
+        dg = eik.DeviceGrid(g)
+        T = torch.tensor(st.T[None], device="cuda")
+        s = torch.tensor(st.s, device="cuda")
+        rec = np.array([g.index(i, j, 0) for i in range(0, n[0], 4) for j in range(0, n[1], 4)], dtype=np.int32)
+        eik.Tangent(dg, T, s, [src], rec=rec).free()          # warm-up (module load, first allocations)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        tan = eik.Tangent(dg, T, s, [src], rec=rec)
+        torch.cuda.synchronize()
+        t_build = time.time() - t0
+        x = tan.stats(0)
+        gen = torch.Generator("cuda").manual_seed(5)
+        p = torch.randn((g.N, 64), device="cuda", generator=gen)
+        y = torch.randn((1, len(rec), 64), device="cuda", generator=gen)
+        for _ in range(3):
+            tan.apply(p, shared_model=True)
+            tan.apply_T(y, sum_sources=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            tan.apply(p, shared_model=True)
+            tan.apply_T(y, sum_sources=True)
+        e1.record()
+        torch.cuda.synchronize()
+        tan.status()
+        ms = e0.elapsed_time(e1) / 10
+        upd = 2.0 * g.N * 64
+        tot_upd += upd
+        tot_ms += ms
+        rows.append({"grid": list(n), "nodes": g.N, "nontrivial_scc": x["nontrivial"], "cyclic_nodes": x["cyclic_nodes"],
+                     "largest_scc": x["largest"], "levels": x["levels"], "tangent_build_ms": round(t_build * 1e3, 2),
+                     "apply_pair_ms": round(ms, 3), "node_updates_per_s": upd / (ms / 1e3)})
+        tan.free()
+    out = {"metric": METRIC, "value": tot_upd / (tot_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": 10, "warmup": 3,
+           "ms_per_step": tot_ms, "higher_is_better": True, "dtype": "f32+f64blocks", "data": "synthetic",
+           "config": {"workload": "Table 3 grids (case C, one source, R 64)", "grids": rows}}
+    print(json.dumps(out), flush=True)
+
+
 def cpu_baseline(wl, n_src: int, R: int = 32) -> dict:
     """The CPU oracle as it stands (single-threaded C, FP64 block traversal) on a bounded
     sample of the workload: `n_src` sources (their states from the oracle's own state
@@ -652,11 +705,11 @@ def main():
     ap.add_argument("--state-cache", default="", help="load/save the solved states (.npy) to skip the state solve")
     ap.add_argument("--gn-max-iters", type=int, default=300)
     ap.add_argument("--cells", action="store_true", help="gn workload: the model on the grid cells")
-    ap.add_argument("--workload", choices=["apply", "lsqr", "gn", "stress", "state"], default="apply",
+    ap.add_argument("--workload", choices=["apply", "lsqr", "gn", "stress", "state", "tables"], default="apply",
                     help="apply: the benchmark line (3-D apply config); lsqr: the 20-iteration Krylov config; "
                          "gn: LSMR on the augmented Gauss-Newton operator (Sec. 4.5); "
                          "stress: the three steep-hill grids with right-hand-side chunking; "
-                         "state: the state solve alone")
+                         "state: the state solve alone; tables: the paper's Table 3 grids")
     ap.add_argument("--lsqr-dtype", choices=["f64", "f32"], default="f64")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
@@ -671,6 +724,8 @@ def main():
         run_stress(args)
     elif args.workload == "state":
         run_state(args)
+    elif args.workload == "tables":
+        run_tables(args)
     else:
         run_ours(args)
 
