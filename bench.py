@@ -622,6 +622,19 @@ def run_tables(args):
     print(json.dumps(out), flush=True)
 
 
+def host_info() -> dict:
+    """The host the oracle is timed on: its hardware threads and CPU model."""
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"host_threads": os.cpu_count(), "cpu_model": model}
+
+
 def cpu_baseline(wl, n_src: int, R: int = 32) -> dict:
     """The CPU oracle as it stands (single-threaded C, FP64 block traversal) on a bounded
     sample of the workload: `n_src` sources (their states from the oracle's own state
@@ -644,7 +657,8 @@ def cpu_baseline(wl, n_src: int, R: int = 32) -> dict:
         t_apply += time.perf_counter() - t0
         upd += 2 * g.N * R
     return {"value": upd / t_apply, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n_src} sources x {R} RHS of the full grid, J and J^T solves, FP64, {t_apply:.1f} s timed"}
+            "sample": f"{n_src} sources x {R} RHS of the full grid, J and J^T solves, FP64, {t_apply:.1f} s timed",
+            **host_info()}
 
 
 def run_reference(args):
@@ -682,7 +696,7 @@ def run_reference(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "sample": f"1 source x {Rs} RHS per step"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"1 source x {Rs} RHS, J and J^T solves per step"},
+                            "sample": f"1 source x {Rs} RHS, J and J^T solves per step", **host_info()},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
