@@ -452,7 +452,8 @@ class GN:
     def lsmr(self, b: torch.Tensor, atol: float = 1e-4, max_iters: int = 200, check_every: int = 5,
              use_graph: bool = True):
         """LSMR until |K^T r| <= atol |K| |r| (checked every `check_every` iterations) or
-        max_iters; returns (x, scalars)."""
+        max_iters; returns (x, scalars).  With use_graph the iterations are replayed from
+        a CUDA graph, which needs a current stream other than the legacy default one."""
         self.start(b)
         done = 0
         while done < max_iters:
