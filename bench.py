@@ -166,8 +166,11 @@ def run_ours(args):
             np.save(cache, T.cpu().numpy())
     torch.cuda.synchronize()
     t_state = time.time() - t0
-    sched = {"persistent": eik.SCHED_PERSISTENT, "levels": eik.SCHED_LEVELS, "staged": eik.SCHED_STAGED}[args.schedule]
-    opts = eik.default_opts(schedule=sched, item_deps=0 if args.level_waits else 1, ctas_per_sm=args.ctas_per_sm)
+    sched = {"persistent": eik.SCHED_PERSISTENT, "levels": eik.SCHED_LEVELS, "staged": eik.SCHED_STAGED,
+             "cluster": eik.SCHED_CLUSTER}[args.schedule]
+    opts = eik.default_opts(schedule=sched, item_deps=0 if args.level_waits else 1, ctas_per_sm=args.ctas_per_sm,
+                            cluster_size=args.cluster_size, cluster_threads=args.cluster_threads,
+                            pass_units=args.pass_units)
     if args.chunk:
         opts.chunk = args.chunk
     t0 = time.time()
@@ -284,7 +287,8 @@ def run_ours(args):
     dom_ms = mf
     achieved = ab[dom] / (dom_ms / 1e3) / 1e9
     kname = {"persistent": "k_traverse_persistent<float,4,%s>", "levels": "k_traverse_level<float,4,%s,1>",
-             "staged": "k_traverse_staged<float,4,%s>"}[args.schedule]
+             "staged": "k_traverse_staged<float,4,%s>",
+             "cluster": "k_traverse_cluster<float,4,%s," + str(args.pass_units or 4) + ">"}[args.schedule]
     kname = kname % ("false" if dom == "fwd" else "true")
     tpu = measured_traffic(dom, kname)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -322,7 +326,7 @@ def run_ours(args):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": upd_step / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * (3 if args.schedule == "persistent" else (2 * max(x["levels"] for x in st) + 3)),
+        "gpu_launches": args.steps * (3 if args.schedule in ("persistent", "cluster") else (2 * max(x["levels"] for x in st) + 3)),
         "clocks": clocks,
         "sweep_baseline": sweep,
         "setup": {"eik_forward_s": round(t_state, 3), "eik_cycles": cyc, "tangent_build_s": round(t_setup, 3),
@@ -707,7 +711,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--schedule", choices=["persistent", "levels", "staged"], default="persistent")
+    ap.add_argument("--schedule", choices=["persistent", "levels", "staged", "cluster"], default="persistent")
+    ap.add_argument("--cluster-size", type=int, default=0, help="cluster schedule: CTAs per cluster (0 = auto)")
+    ap.add_argument("--cluster-threads", type=int, default=0, help="cluster schedule: threads per CTA (0 = 256)")
+    ap.add_argument("--pass-units", type=int, default=0, help="cluster schedule: units per thread per round (2 or 4)")
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0, help="positions per work item (default: the library's, 64)")
     ap.add_argument("--level-waits", action="store_true",

@@ -57,10 +57,13 @@ typedef enum { EIK_MODEL_SLOWNESS = 0, EIK_MODEL_VELOCITY = 1, EIK_MODEL_RELATIV
 typedef enum {
     EIK_SCHED_PERSISTENT = 0,      /* one persistent launch, device level queue, bounded waits */
     EIK_SCHED_LEVELS = 1,          /* one launch per level, replayed from a CUDA graph */
-    EIK_SCHED_STAGED = 2           /* per-level launches whose vector rows are staged in shared
+    EIK_SCHED_STAGED = 2,          /* per-level launches whose vector rows are staged in shared
                                       memory by per-thread async copies (needs R x element size a
                                       multiple of 16 bytes, >= 64, items x 16-byte lanes <= 512
                                       and the two stages within 200 KB; else as LEVELS) */
+    EIK_SCHED_CLUSTER = 3          /* one launch; a thread-block cluster owns one source at a time
+                                      and walks its levels with one hardware cluster barrier per
+                                      level (no device-side spin waits) */
 } eik_schedule;
 
 typedef struct {
@@ -98,6 +101,13 @@ typedef struct {
     int item_deps;             /* 1 (default): a work item waits only for the items holding its
                                   upstream rows; 0: for every item of its source's previous
                                   level (the plain level barrier) */
+    /* cluster schedule */
+    int cluster_size;          /* CTAs per cluster, 1..16 (default 0 = the largest size that keeps
+                                  every source's cluster resident at once) */
+    int cluster_threads;       /* threads per CTA, a multiple of 32 in 64..256 (default 0 = 256) */
+    int pass_units;            /* most right-hand-side vectors a thread of the cluster schedule
+                                  carries for one position: 1, 2 or 4 (default 0 = 4); a thread
+                                  carries 4 / that many positions per round */
 } eik_opts;
 
 typedef struct {

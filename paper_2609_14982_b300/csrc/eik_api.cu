@@ -233,7 +233,7 @@ int tangent_status(eik_tangent *tt, eik_stream stream)
 int tangent_tune(eik_tangent *tt, const eik_opts *o)
 {
     if (!tt || !o) { eik::set_error("bad tangent_tune arguments"); return EIK_ERR_INVALID; }
-    if (o->schedule < EIK_SCHED_PERSISTENT || o->schedule > EIK_SCHED_STAGED) { eik::set_error("bad schedule"); return EIK_ERR_INVALID; }
+    if (o->schedule < EIK_SCHED_PERSISTENT || o->schedule > EIK_SCHED_CLUSTER) { eik::set_error("bad schedule"); return EIK_ERR_INVALID; }
     if (o->rhs_chunk < 0 || o->ctas_per_sm < 0 || !(o->wait_timeout_s > 0)) { eik::set_error("bad tuning values"); return EIK_ERR_INVALID; }
     Tangent *t = tt->impl;
     t->opts.schedule = o->schedule;
@@ -241,6 +241,9 @@ int tangent_tune(eik_tangent *tt, const eik_opts *o)
     t->opts.rhs_chunk = o->rhs_chunk;
     t->opts.wait_timeout_s = o->wait_timeout_s;
     t->opts.item_deps = o->item_deps;
+    t->opts.cluster_size = o->cluster_size;
+    t->opts.cluster_threads = o->cluster_threads;
+    t->opts.pass_units = o->pass_units;
     return EIK_OK;
 }
 

@@ -121,6 +121,12 @@ struct TravParams {
     const double *binv;    // block inverses
     double *ws;
     unsigned long long timeout_ns;
+    // cluster schedule: [S][maxL+1] first position / first block of each level, [S] level
+    // counts, [S] sources in the order clusters take them
+    const int *lvl;
+    const int *blk_lvl;
+    const int *nlev;
+    const int *order;
 };
 
 // ---------------------------------------------------------------- singleton items
@@ -597,6 +603,95 @@ __device__ __forceinline__ void run_stage_singletons(const TravParams &P, const 
     }
 }
 
+// Lane-group form of the same item: a position's lanes (V-element vectors of right-hand
+// sides) are split over G = lanes / W threads; thread (k0, g) takes lanes g, g + G, ...,
+// g + (W-1) G of positions k0 + q * nslot, q < U, decodes each row once for its W lanes
+// and issues all its upstream loads before any sum.  Same arithmetic, in the same order,
+// as run_stage_singletons.
+template <typename T, int V, int W, int U, bool TR>
+__device__ __forceinline__ void run_stage_lanes(const TravParams &P, const ItemStage<T> &S, const unsigned char *tile,
+                                                int lanes)
+{
+    const int G = lanes / W;
+    const int nslot = blockDim.x / G;
+    const int k0 = threadIdx.x / G, g = threadIdx.x - k0 * G;
+    if (k0 >= nslot) return;
+    const long long a = S.it.x;
+    const int p0 = S.it.z, np = S.it.w - S.it.z;
+    const size_t rowb = (size_t)P.R * sizeof(T);
+    const int lo = g * V, ls = G * V;
+    T *x = reinterpret_cast<T *>(P.x) + a * P.N * P.ld_x;
+    const bool J = P.mode == MODE_J;
+    for (int kb = k0; kb < np; kb += U * nslot) {
+        Pack<T, V> xv[U][3][W];
+        int node[U], e0[U], cnt[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int k = kb + q * nslot;
+            node[q] = k < np ? S.perm[k] : -1;
+            cnt[q] = 0;
+            e0[q] = 0;
+            if (node[q] < 0) continue;
+            e0[q] = S.rp[k] - S.ebx;
+            cnt[q] = S.rp[k + 1] - S.rp[k];
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+                if (e < cnt[q]) {
+                    const T *src = x + (long long)S.en[e0[q] + e] * P.ld_x + lo;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) xv[q][e][w] = load_l2<T, V>(src + w * ls);
+                }
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            if (node[q] < 0) continue;
+            const int k = kb + q * nslot;
+            const int rec = S.rec[k];
+            const T c = S.cq[k];
+            const bool has_in = !(TR && J && rec < 0);
+            const T scale = (!TR && J) ? c : T(1);
+            Pack<T, V> acc[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const int r = lo + w * ls;
+                if (tile) {
+                    if (has_in) {
+                        const Pack<T, V> qv = *reinterpret_cast<const Pack<T, V> *>(tile + (size_t)k * rowb + r * sizeof(T));
+#pragma unroll
+                        for (int i = 0; i < V; ++i) acc[w].v[i] = scale * qv.v[i];
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < V; ++i) acc[w].v[i] = T(0);
+                    }
+                } else {
+                    acc[w] = node_input<T, V, TR>(P, (int)a, node[q], rec, c, r);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+                if (e < cnt[q]) {
+                    const T wt = S.ew[e0[q] + e];
+#pragma unroll
+                    for (int w = 0; w < W; ++w)
+#pragma unroll
+                        for (int i = 0; i < V; ++i) acc[w].v[i] += wt * xv[q][e][w].v[i];
+                }
+            for (int e = 3; e < cnt[q]; ++e) {
+                const T wt = S.ew[e0[q] + e];
+                const T *src = x + (long long)S.en[e0[q] + e] * P.ld_x + lo;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    const Pack<T, V> t = load_l2<T, V>(src + w * ls);
+#pragma unroll
+                    for (int i = 0; i < V; ++i) acc[w].v[i] += wt * t.v[i];
+                }
+            }
+#pragma unroll
+            for (int w = 0; w < W; ++w) node_output<T, V, TR>(P, (int)a, node[q], p0 + k, rec, c, lo + w * ls, x, acc[w]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- persistent schedule
 // One launch; CTAs take items by ticket, each CTA in increasing ticket order, and an
 // item waits (bounded) only for lower tickets -- the items holding its upstream rows,
@@ -679,8 +774,8 @@ __device__ __forceinline__ void load_desc(const TravParams &P, ItemStage<T> &S, 
     S.nd = -1;
 }
 
-template <typename T, int V, bool TR>
-__global__ void __launch_bounds__(256, 4) k_traverse_persistent(TravParams P, int G, int tile_bytes)
+template <typename T, int V, bool TR, int W = 0, int U = 1>
+__global__ void __launch_bounds__(256, (W * U >= 4) ? 2 : 4) k_traverse_persistent(TravParams P, int G, int tile_bytes)
 {
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ ItemStage<T> stg[2];
@@ -751,7 +846,10 @@ __global__ void __launch_bounds__(256, 4) k_traverse_persistent(TravParams P, in
         int t2 = 0;
         if (tid == 1 && has_next) t2 = atomicAdd(P.ticket, 1);   // its value is first needed after (B)
         // ---- compute C
-        if (it.z >= 0) run_stage_singletons<T, V, TR>(P, C, tile_bytes ? dyn + b * (size_t)tile_bytes : nullptr, G);
+        if (it.z >= 0) {
+            if (W > 0) run_stage_lanes<T, V, (W > 0 ? W : 1), U, TR>(P, C, tile_bytes ? dyn + b * (size_t)tile_bytes : nullptr, P.R / V);
+            else run_stage_singletons<T, V, TR>(P, C, tile_bytes ? dyn + b * (size_t)tile_bytes : nullptr, G);
+        }
         else run_block<T, TR>(P, it.x, ~it.z);
         __syncthreads();             // (B) every row of C written
         if (tid == 32) {
@@ -771,6 +869,513 @@ __global__ void __launch_bounds__(256, 4) k_traverse_persistent(TravParams P, in
         cp_async_commit();
     }
     cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------- cluster schedule
+// One thread-block cluster of C CTAs owns one (tangent, source) unit at a time and walks
+// its levels in order (reverse order for A^-T).  CTA r of the cluster takes the r-th of C
+// contiguous slices of every level's positions (and every C-th SCC block of the level);
+// after a level every CTA of the cluster meets at one hardware cluster barrier
+// (barrier.cluster arrive.release / wait.acquire), which makes the level's stores visible
+// to the whole cluster before the next level gathers them.  There is no flag and no
+// ticket between levels, and clusters never wait for one another (each unit is a
+// different source), so nothing can deadlock whether or not all clusters are resident.
+// Per CTA the slices are cut into tiles of at most `tp` positions that run through a
+// six-slot pipeline driven by one thread with 1-D bulk copies (cp.async.bulk, completion
+// on an mbarrier per slot and stage):
+//   iteration j issues the row offsets of tile j+5 and, once those have landed, the
+//   structure of tile j+3 (nodes, receiver slots, C*M, upstream positions and weights);
+//   every thread prefetches the input rows of tile j+1 into L2 and computes tile j.
+// Each thread owns one (position, right-hand-side lane) pair per round and U positions
+// per tile, and issues all loads of its U units (input row, up to three upstream rows)
+// before any sum.  The structure and the inputs are never written by the traversal, so
+// they are staged across level barriers; only the upstream rows wait for the barrier.
+constexpr int CL_SLOTS = 6;
+constexpr int CL_EDGE = 6;      // edge capacity per position in a slot (2 x ndim)
+constexpr int CL_MAXTAN = 4;    // tangents per launch
+constexpr int CL_PAD = 8;       // alignment slack (elements) around each staged array
+
+struct ClusterBatch {
+    TravParams P[CL_MAXTAN];
+    int unit_ptr[CL_MAXTAN + 1];   // units of tangent k: [unit_ptr[k], unit_ptr[k+1])
+    int ntan;
+    int tp;                        // tile capacity (positions)
+    int lanes[CL_MAXTAN];          // right-hand-side lanes (R / V) per tangent
+    int tab;                       // capacity of the per-unit level tables (levels + 1)
+    int *ticket;
+};
+
+// slot header; o_* are the element offsets of the first wanted element in each staged
+// array (bulk copies start at the 16-byte granule below it)
+struct ClHdr {
+    int s, q0, np, ne;             // step (>= levels: empty), first position, positions, edges
+    int o_rp, o_pos, o_cq, o_en, o_ew;
+    int pad[3];
+    unsigned long long barA;       // row offsets landed
+    unsigned long long barB;       // structure landed
+};
+
+__device__ __forceinline__ unsigned cl_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cl_ncta()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cl_sync() { cl_arrive(); cl_wait(); }
+// an int in the shared memory of CTA `rank` of this cluster
+__device__ __forceinline__ int cl_load_remote(const int *p, unsigned rank)
+{
+    uint32_t a = smem_u32(p), ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    int v;
+    asm volatile("ld.shared::cluster.b32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
+    return v;
+}
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(unsigned long long *b)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase with the given parity; on time-out the fault is latched and
+// the caller carries on (the copy it waited for can only be late, not lost)
+__device__ __forceinline__ void mbar_wait(unsigned long long *b, unsigned parity, const TravParams &P)
+{
+    if (mbar_try_wait(b, parity)) return;
+    if (*(volatile int *)P.err != 0) return;    // an earlier wait already gave up
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(b, parity)) {
+        if (global_ns() - t0 > P.timeout_ns) {
+            if (atomicCAS(P.err, 0, DEV_TIMEOUT) == 0) { P.err[1] = -1; P.err[2] = -1; P.err[3] = -1; }
+            return;
+        }
+    }
+}
+// 1-D bulk copy global -> this CTA's shared memory, completing on mbarrier b
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *b)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(b)) : "memory");
+}
+
+// Copy elements [i0, i1) of a global array into dst (16-byte aligned) starting at the
+// granule that holds i0; returns the offset of element i0 in dst and adds the bytes.
+template <typename E>
+__device__ __forceinline__ int stage_range(E *dst, const E *src, long long i0, long long i1, unsigned long long *bar)
+{
+    constexpr int G = 16 / sizeof(E);
+    const long long a0 = i0 / G * G, a1 = (i1 + G - 1) / G * G;
+    if (a1 > a0) bulk_g2s(dst, src + a0, (unsigned)((a1 - a0) * sizeof(E)), bar);
+    return (int)(i0 - a0);
+}
+template <typename E>
+__device__ __forceinline__ unsigned range_bytes(long long i0, long long i1)
+{
+    constexpr int G = 16 / sizeof(E);
+    return (unsigned)(((i1 + G - 1) / G * G - i0 / G * G) * sizeof(E));
+}
+
+// layout of one pipeline slot (tp positions, CL_EDGE * tp edges, CL_PAD slack per array)
+template <typename T> struct ClSlot {
+    ClHdr *h;
+    int *rp, *perm, *rec, *en;
+    T *cq, *ew;
+};
+__host__ __device__ __forceinline__ size_t cl_al16(size_t b) { return (b + 15) / 16 * 16; }
+template <typename T>
+__host__ __device__ __forceinline__ size_t cl_slot_bytes(int tp)
+{
+    size_t b = sizeof(ClHdr);
+    b += cl_al16(sizeof(int) * (size_t)(tp + 1 + 2 * CL_PAD));    // rp
+    b += 2 * cl_al16(sizeof(int) * (size_t)(tp + 2 * CL_PAD));    // perm, rec
+    b += cl_al16(sizeof(int) * (size_t)(CL_EDGE * tp + 2 * CL_PAD));   // en
+    b += cl_al16(sizeof(T) * (size_t)(tp + 2 * CL_PAD));          // cq
+    b += cl_al16(sizeof(T) * (size_t)(CL_EDGE * tp + 2 * CL_PAD));     // ew
+    return b;
+}
+template <typename T>
+__device__ __forceinline__ ClSlot<T> cl_slot(unsigned char *base, int tp)
+{
+    ClSlot<T> v;
+    v.h = reinterpret_cast<ClHdr *>(base);
+    size_t o = sizeof(ClHdr);
+    v.rp = reinterpret_cast<int *>(base + o);
+    o += cl_al16(sizeof(int) * (size_t)(tp + 1 + 2 * CL_PAD));
+    v.perm = reinterpret_cast<int *>(base + o);
+    o += cl_al16(sizeof(int) * (size_t)(tp + 2 * CL_PAD));
+    v.rec = reinterpret_cast<int *>(base + o);
+    o += cl_al16(sizeof(int) * (size_t)(tp + 2 * CL_PAD));
+    v.en = reinterpret_cast<int *>(base + o);
+    o += cl_al16(sizeof(int) * (size_t)(CL_EDGE * tp + 2 * CL_PAD));
+    v.cq = reinterpret_cast<T *>(base + o);
+    o += cl_al16(sizeof(T) * (size_t)(tp + 2 * CL_PAD));
+    v.ew = reinterpret_cast<T *>(base + o);
+    return v;
+}
+
+// advance the tile cursor (s, q0, q1) of this CTA through its slices [sh0[s], sh1[s]) of
+// the unit's steps; s = nl when there is no further tile
+__device__ __forceinline__ void cl_next(const int *sh0, const int *sh1, int nl, int tp, int &s, int &q0, int &q1)
+{
+    if (s >= 0 && s < nl && q1 < sh1[s]) {
+        q0 = q1;
+        q1 = min(q0 + tp, sh1[s]);
+        return;
+    }
+    for (++s; s < nl; ++s)
+        if (sh1[s] > sh0[s]) {
+            q0 = sh0[s];
+            q1 = min(q0 + tp, sh1[s]);
+            return;
+        }
+    s = nl;
+    q0 = q1 = 0;
+}
+
+// thread 0, stage A of the next tile: header and its row offsets (rp[q0 .. q1])
+template <typename T>
+__device__ __forceinline__ void cl_stage_a(const TravParams &P, ClSlot<T> v, long long a, const int *sh0, const int *sh1,
+                                           int nl, int tp, int &cs, int &cq0, int &cq1)
+{
+    cl_next(sh0, sh1, nl, tp, cs, cq0, cq1);
+    v.h->s = cs;
+    v.h->q0 = cq0;
+    v.h->np = cq1 - cq0;
+    if (cs >= nl) { mbar_arrive(&v.h->barA); return; }
+    const long long i0 = a * (P.N + 1) + cq0, i1 = a * (P.N + 1) + cq1 + 1;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&v.h->barA, range_bytes<int>(i0, i1));
+    v.h->o_rp = stage_range<int>(v.rp, P.rowptr, i0, i1, &v.h->barA);
+}
+
+// thread 0, stage B (row offsets visible): the structure of the tile
+template <typename T>
+__device__ __forceinline__ void cl_stage_b(const TravParams &P, ClSlot<T> v, long long a, long long ebase, int nl)
+{
+    if (v.h->s >= nl) { mbar_arrive(&v.h->barB); return; }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const int np = v.h->np;
+    const int e0 = v.rp[v.h->o_rp], e1 = v.rp[v.h->o_rp + np];
+    v.h->ne = e1 - e0;
+    const long long p0 = a * P.N + v.h->q0, p1 = p0 + np;
+    const long long g0 = ebase + e0, g1 = ebase + e1;
+    const unsigned bytes = 2 * range_bytes<int>(p0, p1) + range_bytes<T>(p0, p1) + range_bytes<int>(g0, g1) +
+                           range_bytes<T>(g0, g1);
+    mbar_expect_tx(&v.h->barB, bytes);
+    v.h->o_pos = stage_range<int>(v.perm, P.perm, p0, p1, &v.h->barB);
+    stage_range<int>(v.rec, P.rec_slot, p0, p1, &v.h->barB);
+    v.h->o_cq = stage_range<T>(v.cq, reinterpret_cast<const T *>(P.cq), p0, p1, &v.h->barB);
+    v.h->o_en = stage_range<int>(v.en, P.enode, g0, g1, &v.h->barB);
+    v.h->o_ew = stage_range<T>(v.ew, reinterpret_cast<const T *>(P.ew), g0, g1, &v.h->barB);
+}
+
+// Per-source base pointers of a traversal call, so that a unit's addresses are one 32-bit
+// product and one add (every in-source offset is below 2^31: S N R < 2^31 per call).
+template <typename T> struct ClBases {
+    const T *in;     // input rows, indexed by node (forward, raw) or receiver slot (transpose, J)
+    T *x;            // the transported field of the source, canonical order
+    T *out;          // optional natural-order copy
+    T *rec_out;      // forward J: d_rec rows of the source, by receiver slot
+    T *g_out;        // transpose J without the source sum: g rows of the source, by node
+    int ld_in, ld_x, ld_out, ld_aux;
+    bool by_rec;     // input indexed by receiver slot (absent rows are zero)
+    bool scale;      // multiply the input by C*M (forward J)
+};
+
+template <typename T, bool TR>
+__device__ __forceinline__ ClBases<T> cl_bases(const TravParams &P, long long a)
+{
+    ClBases<T> b;
+    const T *in = reinterpret_cast<const T *>(P.in);
+    const bool J = P.mode == MODE_J;
+    b.by_rec = TR && J;
+    b.scale = !TR && J;
+    if (b.by_rec) b.in = in + a * P.n_rec * P.ld_in;
+    else b.in = in + ((!TR && J && P.shared_in) ? 0 : a * P.N * P.ld_in);
+    b.x = reinterpret_cast<T *>(P.x) + a * P.N * P.ld_x;
+    b.out = P.out ? reinterpret_cast<T *>(P.out) + a * P.N * P.ld_out : nullptr;
+    T *aux = reinterpret_cast<T *>(P.aux);
+    b.rec_out = (!TR && J && aux) ? aux + a * P.n_rec * P.ld_aux : nullptr;
+    b.g_out = (TR && J && aux && !P.sum) ? aux + a * P.N * P.ld_aux : nullptr;
+    b.ld_in = (int)P.ld_in;
+    b.ld_x = (int)P.ld_x;
+    b.ld_out = (int)P.ld_out;
+    b.ld_aux = (int)P.ld_aux;
+    return b;
+}
+
+// all threads: the input rows of the tile in slot v (structure visible) into L2
+template <typename T>
+__device__ __forceinline__ void cl_prefetch_input(const ClBases<T> &B, ClSlot<T> v, int nl, int rowb)
+{
+    if (v.h->s >= nl) return;
+    const int np = v.h->np, op = v.h->o_pos;
+    const int lines = (rowb + 127) >> 7;
+    for (int q = threadIdx.x; q < np * lines; q += blockDim.x) {
+        const int k = q / lines, c = q - k * lines;
+        const int row = B.by_rec ? v.rec[op + k] : v.perm[op + k];
+        if (row >= 0 && v.perm[op + k] >= 0)
+            prefetch_l2(reinterpret_cast<const unsigned char *>(B.in + (unsigned)(row * B.ld_in)) + c * 128);
+    }
+}
+
+// all threads: the tile in slot v.  A position's lanes (V-element vectors of right-hand
+// sides) are split over G = lanes / W threads; thread (k0, g) handles lanes g, g + G, ...,
+// g + (W-1) G of positions k0 + q * kstep, q < U = 4 / W.  The row of a position is
+// decoded once per thread and shared by its W lanes, and every load of the thread (input
+// rows, up to three upstream rows) is issued before any sum.
+template <typename T, int V, int W, bool TR>
+__device__ __forceinline__ void cl_compute(const ClBases<T> &B, ClSlot<T> v, int k0, int g, int kstep, int G)
+{
+    constexpr int U = 4 / W;
+    const int np = v.h->np, p0 = v.h->q0;
+    const int orp = v.h->o_rp, op = v.h->o_pos, ocq = v.h->o_cq, oen = v.h->o_en, oew = v.h->o_ew;
+    const int ebx = v.rp[orp];
+    const int lo = g * V, ls = G * V;      // element offset of the first lane, lane stride
+    Pack<T, V> in[U][W], up[U][3][W];
+    int node[U], e0[U], cnt[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+        const int k = k0 + q * kstep;
+        node[q] = k < np ? v.perm[op + k] : -1;
+        cnt[q] = 0;
+        e0[q] = 0;
+        if (node[q] < 0) continue;
+        const int r0 = v.rp[orp + k];
+        e0[q] = r0 - ebx;
+        cnt[q] = v.rp[orp + k + 1] - r0;
+        const int row = B.by_rec ? v.rec[op + k] : node[q];
+        if (row >= 0) {
+            const T *src = B.in + (unsigned)(row * B.ld_in + lo);
+#pragma unroll
+            for (int w = 0; w < W; ++w) in[q][w] = load_l2<T, V>(src + w * ls);
+        } else {
+#pragma unroll
+            for (int w = 0; w < W; ++w)
+#pragma unroll
+                for (int i = 0; i < V; ++i) in[q][w].v[i] = T(0);
+        }
+#pragma unroll
+        for (int e = 0; e < 3; ++e)
+            if (e < cnt[q]) {
+                const T *src = B.x + (unsigned)(v.en[oen + e0[q] + e] * B.ld_x + lo);
+#pragma unroll
+                for (int w = 0; w < W; ++w) up[q][e][w] = load_l2<T, V>(src + w * ls);
+            }
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+        if (node[q] < 0) continue;
+        const int k = k0 + q * kstep;
+        const T c = v.cq[ocq + k];
+        const T scale = B.scale ? c : T(1);
+        Pack<T, V> acc[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+#pragma unroll
+            for (int i = 0; i < V; ++i) acc[w].v[i] = scale * in[q][w].v[i];
+#pragma unroll
+        for (int e = 0; e < 3; ++e)
+            if (e < cnt[q]) {
+                const T wt = v.ew[oew + e0[q] + e];
+#pragma unroll
+                for (int w = 0; w < W; ++w)
+#pragma unroll
+                    for (int i = 0; i < V; ++i) acc[w].v[i] += wt * up[q][e][w].v[i];
+            }
+        for (int e = 3; e < cnt[q]; ++e) {
+            const T wt = v.ew[oew + e0[q] + e];
+            const T *src = B.x + (unsigned)(v.en[oen + e0[q] + e] * B.ld_x + lo);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const Pack<T, V> xv = load_l2<T, V>(src + w * ls);
+#pragma unroll
+                for (int i = 0; i < V; ++i) acc[w].v[i] += wt * xv.v[i];
+            }
+        }
+        T *dst = B.x + (unsigned)((p0 + k) * B.ld_x + lo);
+#pragma unroll
+        for (int w = 0; w < W; ++w) store<T, V>(dst + w * ls, acc[w]);
+        if (B.out) {
+            T *o = B.out + (unsigned)(node[q] * B.ld_out + lo);
+#pragma unroll
+            for (int w = 0; w < W; ++w) store<T, V>(o + w * ls, acc[w]);
+        }
+        if (B.rec_out) {
+            const int rs = v.rec[op + k];
+            if (rs >= 0) {
+                T *o = B.rec_out + (unsigned)(rs * B.ld_aux + lo);
+#pragma unroll
+                for (int w = 0; w < W; ++w) store<T, V>(o + w * ls, acc[w]);
+            }
+        } else if (B.g_out) {
+            T *o = B.g_out + (unsigned)(node[q] * B.ld_aux + lo);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                Pack<T, V> gv;
+#pragma unroll
+                for (int i = 0; i < V; ++i) gv.v[i] = c * acc[w].v[i];
+                store<T, V>(o + w * ls, gv);
+            }
+        }
+    }
+}
+
+// SCC blocks are rare; kept out of line so their registers do not weigh on the tile loop
+template <typename T, bool TR>
+__device__ __noinline__ void cl_block(const TravParams &P, int a, int b)
+{
+    run_block<T, TR>(P, a, b);
+}
+
+template <typename T, int V, bool TR, int W>
+__global__ void __launch_bounds__(256, 2) k_traverse_cluster(const __grid_constant__ ClusterBatch B)
+{
+    extern __shared__ __align__(128) unsigned char dyn[];
+    __shared__ int s_unit;
+    __shared__ TravParams sP;
+    const unsigned C = cl_ncta(), rank = cl_rank();
+    const int tid = threadIdx.x;
+    const int tp = B.tp;
+    const size_t sb = cl_slot_bytes<T>(tp);
+    int *sh0 = reinterpret_cast<int *>(dyn + CL_SLOTS * sb);   // this CTA's slice of every step
+    int *sh1 = sh0 + B.tab;
+    int *tab_blk = sh1 + B.tab;                                  // first block of every level
+    auto slot = [&](int j) { return cl_slot<T>(dyn + (size_t)(j % CL_SLOTS) * sb, tp); };
+    if (tid == 0)
+        for (int q = 0; q < CL_SLOTS; ++q) {
+            ClSlot<T> v = slot(q);
+            mbar_init(&v.h->barA, 1);
+            mbar_init(&v.h->barB, 1);
+        }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+    int uses = 0;   // tiles run through the slots so far (mbarrier phases)
+    for (;;) {
+        if (rank == 0 && tid == 0) s_unit = atomicAdd(B.ticket, 1);
+        cl_sync();
+        const int u = cl_load_remote(&s_unit, 0);
+        cl_sync();                       // every CTA has read the ticket before rank 0 takes the next
+        if (u >= B.unit_ptr[B.ntan]) break;
+        int k = 0;
+        while (u >= B.unit_ptr[k + 1]) ++k;
+        {
+            const int *src = reinterpret_cast<const int *>(&B.P[k]);
+            int *dst = reinterpret_cast<int *>(&sP);
+            for (int i = tid; i < (int)(sizeof(TravParams) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();
+        const TravParams &P = sP;
+        const int lanes = B.lanes[k];
+        const long long a = __ldg(P.order + (u - B.unit_ptr[k]));
+        const int nl = __ldg(P.nlev + a);
+        const long long ebase = __ldg(P.ebase + a);
+        {
+            const int *lvl = P.lvl + a * (P.maxL + 1);
+            for (int i = tid; i <= nl; i += blockDim.x) {
+                tab_blk[i] = __ldg(P.blk_lvl + a * (P.maxL + 1) + i);
+                if (i < nl) {
+                    const int L = TR ? nl - 1 - i : i;
+                    const int lo = __ldg(lvl + L), n = __ldg(lvl + L + 1) - lo;
+                    sh0[i] = lo + n * (int)rank / (int)C;          // n * 16 < 2^31: int arithmetic
+                    sh1[i] = lo + n * ((int)rank + 1) / (int)C;
+                }
+            }
+        }
+        // this thread's (position, lane group) and the tile size
+        const int G = lanes / W;
+        const int kstep = blockDim.x / G;
+        const int k0 = tid / G, g = tid - k0 * G;
+        const int tpu = min(tp, (4 / W) * kstep);
+        const ClBases<T> bases = cl_bases<T, TR>(P, a);
+        const int rowb = P.R * (int)sizeof(T);
+        __syncthreads();
+        // pipeline over this CTA's tiles; tile j uses slot (uses + j) % CL_SLOTS, and the
+        // n-th use of a slot waits for mbarrier phase parity n & 1
+        auto sl = [&](int j) { return slot(uses + j); };
+        auto par = [&](int j) { return (unsigned)(((uses + j) / CL_SLOTS) & 1); };
+        int cs = -1, cq0 = 0, cq1 = 0;     // tile cursor (thread 0)
+        // prologue: row offsets of tiles 0..4, structure of tiles 0..2; visible before
+        // iteration 0: the structure of tiles 0, 1 and the row offsets of tiles 0..3
+        if (tid == 0) {
+            for (int q = 0; q < 5; ++q) cl_stage_a<T>(P, sl(q), a, sh0, sh1, nl, tpu, cs, cq0, cq1);
+            for (int q = 0; q < 3; ++q) {
+                mbar_wait(&sl(q).h->barA, par(q), P);
+                cl_stage_b<T>(P, sl(q), a, ebase, nl);
+            }
+            for (int q = 0; q < 2; ++q) mbar_wait(&sl(q).h->barB, par(q), P);
+            mbar_wait(&sl(3).h->barA, par(3), P);
+        }
+        __syncthreads();
+        cl_prefetch_input<T>(bases, sl(0), nl, rowb);
+        int j = 0;
+        for (int s = 0; s < nl; ++s) {
+            for (;;) {
+                ClSlot<T> cur = sl(j);
+                if (cur.h->s != s) break;
+                // visible here: the structure of tiles j, j+1 and the row offsets of tiles
+                // up to j+3 (stage B of tile j+2 and stage A of tile j+4 were issued one
+                // iteration ago)
+                cl_prefetch_input<T>(bases, sl(j + 1), nl, rowb);
+                if (tid == 0) {
+                    cl_stage_b<T>(P, sl(j + 3), a, ebase, nl);
+                    cl_stage_a<T>(P, sl(j + 5), a, sh0, sh1, nl, tpu, cs, cq0, cq1);
+                }
+                if (k0 < kstep) cl_compute<T, V, W, TR>(bases, cur, k0, g, kstep, G);
+                if (tid == 0) {
+                    mbar_wait(&sl(j + 2).h->barB, par(j + 2), P);
+                    mbar_wait(&sl(j + 4).h->barA, par(j + 4), P);
+                }
+                __syncthreads();             // staged data visible; slot j is free
+                ++j;
+            }
+            const int L = TR ? nl - 1 - s : s;
+            for (int b = tab_blk[L] + (int)rank; b < tab_blk[L + 1]; b += C) cl_block<T, TR>(P, (int)a, b);
+            cl_sync();
+        }
+        // tile indices j .. j+4 are empty: stage A has arrived on all of them, stage B on
+        // j .. j+2; arrive stage B of the last two so that every index used each of its
+        // slot's barriers exactly once, then advance the slots past them
+        if (tid == 0) {
+            cl_stage_b<T>(P, sl(j + 3), a, ebase, nl);
+            cl_stage_b<T>(P, sl(j + 4), a, ebase, nl);
+        }
+        uses += j + 5;
+        __syncthreads();
+    }
+    if (tid == 0)
+        for (int q = 0; q < CL_SLOTS; ++q) {
+            ClSlot<T> v = slot(q);
+            mbar_inval(&v.h->barA);
+            mbar_inval(&v.h->barB);
+        }
 }
 
 // g[j][r] = sum_a cq_a[j] lam_a[j][r] in source order.  FP64 path: FP64 products and
@@ -960,9 +1565,105 @@ static int launch_staged(Tangent *t, int G, int threads, size_t dyn, int per_sm,
     return EIK_OK;
 }
 
+template <typename T, int V, bool TR, int W>
+static int launch_cluster_u(Tangent *t, ClusterBatch &B, int units, cudaStream_t st)
+{
+    auto kern = k_traverse_cluster<T, V, TR, W>;
+    const int threads = t->opts.cluster_threads > 0 ? t->opts.cluster_threads : 256;
+    const size_t dyn = CL_SLOTS * cl_slot_bytes<T>(B.tp) + 3 * (size_t)B.tab * sizeof(int);
+    if (dyn > 200 * 1024) { set_error("cluster schedule: %zu bytes of shared memory needed", dyn); return EIK_ERR_INVALID; }
+    EIK_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    EIK_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = dyn;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    // active clusters of size c (cached per launch shape)
+    auto fit = [&](int c, int *n) -> int {
+        const long long key = ((long long)TR << 62) | ((long long)sizeof(T) << 56) | ((long long)V << 52) |
+                              ((long long)W << 48) | ((long long)threads << 36) | ((long long)dyn << 8) | c;
+        auto it = t->cluster_fit.find(key);
+        if (it != t->cluster_fit.end()) { *n = it->second; return EIK_OK; }
+        at[0].val.clusterDim.x = (unsigned)c;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)c);
+        int m = 0;
+        cudaError_t e = cudaOccupancyMaxActiveClusters(&m, kern, &cfg);
+        if (e != cudaSuccess) { cudaGetLastError(); m = 0; }
+        t->cluster_fit[key] = m;
+        *n = m;
+        return EIK_OK;
+    };
+    int C = t->opts.cluster_size, nact = 0;
+    if (C > 0) {
+        fit(C, &nact);
+    } else {
+        // the largest cluster that keeps every unit resident at once, else the size with the
+        // most CTAs in flight
+        static const int sizes[] = {16, 12, 8, 6, 4, 2, 1};
+        int best = 1, best_ctas = -1;
+        for (int c : sizes) {
+            int m = 0;
+            fit(c, &m);
+            if (m >= units) { C = c; nact = m; break; }
+            if (m * c > best_ctas) { best_ctas = m * c; best = c; nact = m; }
+        }
+        if (C <= 0) C = best;
+    }
+    if (nact <= 0) { set_error("cluster schedule: no cluster of %d CTAs x %d threads fits", C, threads); return EIK_ERR_INVALID; }
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(std::min(units, nact) * C));
+    EIK_CHECK(cudaMemsetAsync(B.ticket, 0, sizeof(int), st));
+    EIK_CHECK(cudaLaunchKernelEx(&cfg, kern, B));
+    return EIK_OK;
+}
+
+template <typename T, int V, bool TR>
+static int launch_cluster(Tangent *t, const TravParams &P, cudaStream_t st)
+{
+    if (t->opts.cluster_threads != 0 &&
+        (t->opts.cluster_threads < 64 || t->opts.cluster_threads > 256 || t->opts.cluster_threads % 32)) {
+        set_error("cluster_threads must be a multiple of 32 in 64..256");
+        return EIK_ERR_INVALID;
+    }
+    if (t->opts.cluster_size < 0 || t->opts.cluster_size > 16) { set_error("cluster_size must be 0..16"); return EIK_ERR_INVALID; }
+    ClusterBatch B{};
+    B.P[0] = P;
+    B.ntan = 1;
+    B.unit_ptr[0] = 0;
+    B.unit_ptr[1] = t->S;
+    B.lanes[0] = P.R / V;
+    const int threads = t->opts.cluster_threads > 0 ? t->opts.cluster_threads : 256;
+    if (B.lanes[0] > threads) {
+        set_error("cluster schedule: %d right-hand-side lanes exceed %d threads per CTA; set rhs_chunk", B.lanes[0], threads);
+        return EIK_ERR_INVALID;
+    }
+    // lanes per thread: the widest of 4, 2, 1 that divides the lanes (pass_units caps it)
+    const int cap = t->opts.pass_units > 0 ? t->opts.pass_units : 4;
+    int W = 1;
+    if (cap >= 4 && B.lanes[0] % 4 == 0) W = 4;
+    else if (cap >= 2 && B.lanes[0] % 2 == 0) W = 2;
+    B.tp = std::min(512, (4 / W) * (threads / (B.lanes[0] / W)));
+    B.tab = t->maxL + 1;
+    // keep the six slots and the level tables within 160 KB of shared memory
+    while (B.tp > 32 && CL_SLOTS * cl_slot_bytes<T>(B.tp) + 3 * (size_t)B.tab * sizeof(int) > 160 * 1024) B.tp /= 2;
+    B.ticket = t->ticket + 1;
+    if (W == 4) return launch_cluster_u<T, V, TR, 4>(t, B, t->S, st);
+    if (W == 2) return launch_cluster_u<T, V, TR, 2>(t, B, t->S, st);
+    return launch_cluster_u<T, V, TR, 1>(t, B, t->S, st);
+}
+
 template <typename T, int V, bool TR>
 static int launch_traverse(Tangent *t, TravParams &P, int G, cudaStream_t st)
 {
+    if (t->opts.schedule == EIK_SCHED_CLUSTER) return launch_cluster<T, V, TR>(t, P, st);
     const size_t rowb = (size_t)P.R * sizeof(T);
     const bool staged_ok = rowb % 16 == 0 && rowb >= 64 && (P.ld_in * sizeof(T)) % 16 == 0 &&
                            (P.ld_x * sizeof(T)) % 16 == 0 && V * sizeof(T) == 16;
@@ -1041,10 +1742,18 @@ static int launch_traverse(Tangent *t, TravParams &P, int G, cudaStream_t st)
                       ((uintptr_t)P.in & 15) == 0 && (size_t)t->item_max * rowb <= 32768;
     const int tile_bytes = tile ? (int)(t->item_max * rowb) : 0;
     const size_t dyn = 2 * (size_t)tile_bytes;
-    EIK_CHECK(cudaFuncSetAttribute(k_traverse_persistent<T, V, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    // compute form: one vector per thread (default), or lane groups of W = pass_units vectors
+    // per thread when W divides the lanes (measured slower on the 3-D apply workload: the
+    // item is bound by dependent-instruction and memory latency, not by instruction count)
+    const int lanes = P.R / V;
+    const int want = t->opts.pass_units > 0 ? t->opts.pass_units : 1;
+    void (*kern)(TravParams, int, int) = k_traverse_persistent<T, V, TR>;
+    if (want >= 4 && lanes % 4 == 0 && lanes / 4 <= threads) kern = k_traverse_persistent<T, V, TR, 4, 1>;
+    else if (want >= 2 && lanes % 2 == 0 && lanes / 2 <= threads) kern = k_traverse_persistent<T, V, TR, 2, 1>;
+    EIK_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = t->opts.ctas_per_sm;
     if (per_sm <= 0) {
-        EIK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_persistent<T, V, TR>, threads, dyn));
+        EIK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, dyn));
         per_sm = std::max(per_sm, 1);
     }
     long long grid = std::min<long long>((long long)t->num_sms * per_sm, P.nitems);
@@ -1052,7 +1761,7 @@ static int launch_traverse(Tangent *t, TravParams &P, int G, cudaStream_t st)
     EIK_CHECK(cudaMemsetAsync(P.done, 0, (size_t)t->S * t->maxL * sizeof(int), st));
     EIK_CHECK(cudaMemsetAsync(P.ticket, 0, sizeof(int), st));
     EIK_CHECK(cudaMemsetAsync(P.item_done, 0, (size_t)std::max(P.nitems, 1) * sizeof(int), st));
-    k_traverse_persistent<T, V, TR><<<(unsigned)grid, threads, dyn, st>>>(P, G, tile_bytes);
+    kern<<<(unsigned)grid, threads, dyn, st>>>(P, G, tile_bytes);
     EIK_CHECK_LAUNCH();
     return EIK_OK;
 }
@@ -1166,6 +1875,7 @@ int traverse(Tangent *t, bool TR, int mode, const void *in, int shared_in, int R
         P.item_done = t->item_done;
         P.blk_desc = t->blk_desc; P.blk_off = t->blk_off; P.binv = t->binv; P.ws = t->ws_blk;
         P.timeout_ns = (unsigned long long)(t->opts.wait_timeout_s * 1e9);
+        P.lvl = t->lvl_d; P.blk_lvl = t->blk_lvl_d; P.nlev = t->nlev_d; P.order = t->order_d;
         if (dtype == EIK_F32) rc = TR ? dispatch_v<float, true>(t, P, st) : dispatch_v<float, false>(t, P, st);
         else rc = TR ? dispatch_v<double, true>(t, P, st) : dispatch_v<double, false>(t, P, st);
         if (rc) return rc;

@@ -124,6 +124,14 @@ struct Tangent {
     int *done = nullptr;          // [S][maxL] completed items per (source, step)
     int *ticket = nullptr;        // [2]
     int *err = nullptr;           // [4] device fault latch {code, source, step, item}
+    // cluster schedule: per source the first position of every level and the first block of
+    // every level (blocks are ordered by (source, level)), and the sources by decreasing level
+    // count (the order in which clusters take them)
+    int *lvl_d = nullptr;         // [S][maxL+1]
+    int *blk_lvl_d = nullptr;     // [S][maxL+1]
+    int *nlev_d = nullptr;        // [S]
+    int *order_d = nullptr;       // [S]
+    std::map<long long, int> cluster_fit;   // cached occupancy queries of the cluster launch
     // off-grid receivers (multilinear sampling), set by tangent_set_receivers
     int n_ip = 0, ip_k = 0;       // receivers per source, corners per receiver (2^ndim)
     int *ip_node = nullptr;       // [S][n_ip][ip_k] natural node of each corner

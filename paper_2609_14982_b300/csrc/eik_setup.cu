@@ -804,8 +804,10 @@ struct Scratch {
     }
 };
 
+// Tangent arrays carry 64 bytes of tail padding: the traversal stages slices of them with
+// 16-byte-granular bulk copies whose last granule may extend past the final element.
 template <typename T>
-cudaError_t dalloc(T **p, size_t n) { return cudaMalloc((void **)p, std::max<size_t>(n, 1) * sizeof(T)); }
+cudaError_t dalloc(T **p, size_t n) { return cudaMalloc((void **)p, std::max<size_t>(n, 1) * sizeof(T) + 64); }
 
 inline unsigned blocks_for(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
@@ -820,7 +822,7 @@ void free_tangent(Tangent *t)
                     t->binv, t->piv, t->items_fwd, t->items_bwd, t->ebeg_fwd, t->ebeg_bwd, t->deps_fwd, t->deps_bwd,
                     t->ndeps_fwd, t->ndeps_bwd, t->item_done, t->item_cnt, t->done, t->ticket, t->err, t->ws_vec,
                     t->ws_blk, t->ebase_d, t->tbase_d, t->ip_node, t->ip_w, t->ipt_node, t->ipt_ptr, t->ipt_e,
-                    t->ws_in};
+                    t->ws_in, t->lvl_d, t->blk_lvl_d, t->nlev_d, t->order_d};
     for (void *p : ptrs) if (p) cudaFree(p);
     if (t->params_d) cudaFree((void *)t->params_d);
     for (auto &kv : t->level_graphs) if (kv.second) cudaGraphExecDestroy(kv.second);
@@ -1232,6 +1234,30 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
         k_item_deps<<<blocks_for(ni), 256, 0, st>>>(ni, N, t->items_bwd, t->blk_desc, t->perm, t->cptr, t->dn_node,
                                                     t->tbase_d, iop, t->deps_bwd, t->ndeps_bwd);
         TRY(cudaGetLastError());
+        // cluster schedule tables
+        std::vector<int> hl_pos((size_t)S * (maxL + 1), 0), hb_lvl((size_t)S * (maxL + 1), 0), hn(S), ord(S);
+        size_t bj = 0;
+        for (int a = 0; a < S; ++a) {
+            hn[a] = t->nlev[a];
+            for (int L = 0; L <= maxL; ++L) {
+                const int Lc = std::min(L, t->nlev[a]);
+                hl_pos[(size_t)a * (maxL + 1) + L] = (int)t->level_ptr[(size_t)a * (maxL + 1) + Lc];
+                while (bj < t->blocks.size() && (t->blocks[bj].src < a || (t->blocks[bj].src == a && t->blocks[bj].level < L)))
+                    ++bj;
+                hb_lvl[(size_t)a * (maxL + 1) + L] = (int)bj;
+            }
+        }
+        for (int a = 0; a < S; ++a) ord[a] = a;
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return t->nlev[x] > t->nlev[y]; });
+        TRY(dalloc(&t->lvl_d, hl_pos.size()));
+        TRY(dalloc(&t->blk_lvl_d, hb_lvl.size()));
+        TRY(dalloc(&t->nlev_d, S));
+        TRY(dalloc(&t->order_d, S));
+        TRY(cudaMemcpyAsync(t->lvl_d, hl_pos.data(), hl_pos.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        TRY(cudaMemcpyAsync(t->blk_lvl_d, hb_lvl.data(), hb_lvl.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        TRY(cudaMemcpyAsync(t->nlev_d, hn.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
+        TRY(cudaMemcpyAsync(t->order_d, ord.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
+        TRY(cudaStreamSynchronize(st));   // the host vectors above go out of scope
     }
 
     // ---- statistics

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libeik.so")
 
 EIK_F64, EIK_F32 = 0, 1
 MODEL_SLOWNESS, MODEL_VELOCITY, MODEL_RELATIVE = 0, 1, 2
-SCHED_PERSISTENT, SCHED_LEVELS, SCHED_STAGED = 0, 1, 2
+SCHED_PERSISTENT, SCHED_LEVELS, SCHED_STAGED, SCHED_CLUSTER = 0, 1, 2, 3
 STATUS = {0: "OK", -1: "INVALID", -2: "OOM", -3: "SINGULAR_BLOCK", -4: "NOT_CONVERGED", -5: "TIMEOUT",
           -6: "CUDA", -7: "CYCLE"}
 
@@ -46,7 +46,8 @@ class Opts(C.Structure):
                 ("chunk", C.c_int), ("ctas_per_sm", C.c_int), ("wait_timeout_s", C.c_double),
                 ("eik_tol", C.c_double), ("eik_max_cycles", C.c_int), ("eik_src_radius", C.c_double),
                 ("sweep_tol", C.c_double), ("sweep_max_cycles", C.c_int), ("rhs_chunk", C.c_int),
-                ("eik_fp32", C.c_int), ("eik_fp64_radius", C.c_double), ("item_deps", C.c_int)]
+                ("eik_fp32", C.c_int), ("eik_fp64_radius", C.c_double), ("item_deps", C.c_int),
+                ("cluster_size", C.c_int), ("cluster_threads", C.c_int), ("pass_units", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -323,9 +324,11 @@ class Tangent:
         return out, cyc.value
 
     def tune(self, **kw):
-        """Change run-time options (schedule, ctas_per_sm, rhs_chunk, wait_timeout_s, item_deps)."""
+        """Change run-time options (schedule, ctas_per_sm, rhs_chunk, wait_timeout_s, item_deps,
+        cluster_size, cluster_threads, pass_units)."""
         for k, v in kw.items():
-            if k not in ("schedule", "ctas_per_sm", "rhs_chunk", "wait_timeout_s", "item_deps"):
+            if k not in ("schedule", "ctas_per_sm", "rhs_chunk", "wait_timeout_s", "item_deps", "cluster_size",
+                         "cluster_threads", "pass_units"):
                 raise KeyError(k)
             setattr(self.opts, k, v)
         _check(lib().tangent_tune(self.h, C.byref(self.opts)))
