@@ -159,14 +159,18 @@ int eik_forward(const eik_grid *g, const double *s, int S, const int *src_node,
  * allocator: its scratch is one file-scope device array of
  * eik_forward_noalloc_capacity() bytes (64 MiB), held by every GPU that loads the
  * library until the process exits.
- *   Limit: the call needs 2 N ndim^2 + S N (2 + 2 ndim) doubles + S N bytes (+ small
- *   alignment); larger requests return EIK_ERR_INVALID with the sizes in the message
- *   (about 320k 3-D nodes for one source).
+ *   Limit: the call needs 2 N ndim^2 + S N (2 + 2 ndim) doubles + S N bytes + S x 8 KiB
+ *   (the per-source convergence slots: 1024 64-bit words each) + S x 13 bytes, each
+ *   piece rounded up to 256 bytes; larger requests return EIK_ERR_INVALID with the sizes
+ *   in the message (about 320k 3-D nodes for one source).
  *   Set-up: the first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call before any
- *   stream capture.
+ *   (cudaGetSymbolAddress) with that device current and keeps it for the life of the
+ *   process; make that first call before any stream capture, and do not use this call
+ *   across a cudaDeviceReset of that device (the array moves, the kept address does not).
  *   Sharing: every call, on any stream, uses the same array and overwrites it; calls
- *   that overlap on the GPU race with each other.  Issue them one after the other.
+ *   that overlap on the GPU race with each other.  Issue them one after the other.  A
+ *   call that returns an error has first waited for its own queued work, so a following
+ *   call does not race with it.
  */
 int eik_forward_noalloc(const eik_grid *g, const double *s, int S, const int *src_node,
                         double *T, const eik_opts *opts, int *cycles, eik_stream stream);
@@ -215,10 +219,13 @@ int tangent_apply(eik_tangent *t, const void *p, int shared_model, int R,
  * 17-18): r = P^T y, lam = A^-T r by the reverse block traversal B_a^T (U^T, L^T, P^T
  * on blocks), g_a = M^T C^T lam_a, and g = sum_a g_a when sum_sources.
  *   y            device [S][n_rec][R]
+ *   sum_sources  0: g_a per source; 1: g = sum_a g_a; 2: g += sum_a g_a (accumulates
+ *                over calls, e.g. over source chunks of one gradient)
  *   g            device [N][R] if sum_sources else [S][N][R]
  *   lam_full     device [S][N][R] or NULL (internal workspace)
  * The source sum is a deterministic reduction in source order (EIK_F64: FP64;
- * EIK_F32: FP32 products with a compensated FP32 sum).
+ * EIK_F32: FP32 products with a compensated FP32 sum); with sum_sources = 2 the call's
+ * sum is then added to g.
  */
 int tangent_apply_T(eik_tangent *t, const void *y, int R, int sum_sources,
                     void *g, void *lam_full, int dtype, eik_stream stream);
@@ -404,6 +411,9 @@ int gn_create_cells(eik_tangent *t, const double *wd, const double *v_cells, dou
 int gn_dims(const eik_gn *g, int64_t *n_rows, int64_t *n_data, int64_t *n_rough);
 int gn_apply(eik_gn *g, const void *p, void *out, eik_stream stream);
 int gn_apply_T(eik_gn *g, const void *y, void *out, eik_stream stream);
+/* gn_rhs: the right-hand side b = [-W_d r; 0; 0] of Eq. (augmented-ls) for a data
+ * residual r (device FP64 [S][n_rec]) into b (device [n_rows], the solver's dtype). */
+int gn_rhs(eik_gn *g, const double *r, void *b, eik_stream stream);
 int gn_lsmr_start(eik_gn *g, const void *b, eik_stream stream);
 int gn_lsmr_iterate(eik_gn *g, int iters, int use_graph, eik_stream stream);
 int gn_lsmr_solution(eik_gn *g, void *x, double *scalars, eik_stream stream);

@@ -509,7 +509,10 @@ extern "C" int eik_forward_noalloc(const eik_grid *gin, const double *s, int S, 
         unsigned char *active = carve((size_t)S);
         double *t0_fp64 = (double *)carve((size_t)S * sizeof(double));
         cudaStream_t st = (cudaStream_t)stream;
-#define TRY(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return cuda_fail(e_, #call, __FILE__, __LINE__); } while (0)
+        // on a failure after work was queued, wait for that work before returning: the next
+        // call reuses the same scratch array and must not race with leftovers of this one
+#define TRY(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { cudaStreamSynchronize(st); cudaGetLastError(); \
+                                                                      return cuda_fail(e_, #call, __FILE__, __LINE__); } } while (0)
         TRY(cudaMemcpyAsync(src_d, src_node, S * sizeof(int), cudaMemcpyHostToDevice, st));
         double hmax = 0.0;
         for (int d = 0; d < nd; ++d) hmax = std::max(hmax, g.dxi[d]);

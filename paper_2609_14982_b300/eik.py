@@ -28,7 +28,7 @@ EXPORTED = ["eik_opts_default", "eik_last_error", "eik_version", "eik_forward", 
             "eik_forward_noalloc", "eik_forward_noalloc_capacity",
             "gn_create", "gn_dims", "gn_apply", "gn_apply_T", "gn_lsmr_start", "gn_lsmr_iterate",
             "gn_lsmr_solution", "gn_free", "model_cells_to_nodes", "model_nodes_to_cells",
-            "tangent_set_receivers", "tangent_apply_interp", "tangent_apply_interp_T", "gn_create_cells"]
+            "tangent_set_receivers", "tangent_apply_interp", "tangent_apply_interp_T", "gn_create_cells", "gn_rhs"]
 
 
 class EikError(RuntimeError):
@@ -101,6 +101,7 @@ def lib():
         L.gn_apply.argtypes = [P, P, P, P]
         L.gn_apply_T.argtypes = [P, P, P, P]
         L.gn_lsmr_start.argtypes = [P, P, P]
+        L.gn_rhs.argtypes = [P, P, P, P]
         L.gn_lsmr_iterate.argtypes = [P, I, I, P]
         L.gn_lsmr_solution.argtypes = [P, P, P, P]
         L.gn_free.argtypes = [P]
@@ -194,10 +195,25 @@ def nodes_to_cells(dgrid: DeviceGrid, g_node: torch.Tensor) -> torch.Tensor:
     return out if g_node.dim() == 2 else out[:, 0]
 
 
+def _check_state_args(dgrid: DeviceGrid, s: torch.Tensor, S: int, out: torch.Tensor | None):
+    """Shapes and devices of a state solve, checked before any pointer reaches the library:
+    s has N entries, out is [S, N], and s, out and the grid live on the current device."""
+    if int(s.numel()) != dgrid.N:
+        raise ValueError(f"s has {int(s.numel())} entries, the grid has {dgrid.N} nodes")
+    if out is not None and tuple(out.shape) != (S, dgrid.N):
+        raise ValueError(f"out must be [{S}, {dgrid.N}], got {list(out.shape)}")
+    if s.is_cuda:
+        cur = torch.cuda.current_device()
+        for name, t in (("s", s), ("out", out), ("grid", dgrid.xyz)):
+            if t is not None and t.is_cuda and t.device.index != cur:
+                raise ValueError(f"{name} is on {t.device}, the current device is cuda:{cur}")
+
+
 def eik_forward(dgrid: DeviceGrid, s: torch.Tensor, src, opts: Opts | None = None, out: torch.Tensor | None = None):
     """First-arrival traveltimes [S, N] (float64) for the given source nodes."""
     src = torch.as_tensor(src, dtype=torch.int32).contiguous().cpu()
     S = int(src.numel())
+    _check_state_args(dgrid, s, S, out)
     if out is None:
         out = torch.empty((S, dgrid.N), dtype=torch.float64, device=s.device)
     cyc = C.c_int(0)
@@ -210,6 +226,7 @@ def eik_forward_noalloc(dgrid: DeviceGrid, s: torch.Tensor, src, out: torch.Tens
     """Same result as eik_forward, without any device allocation inside the library: the
     caller provides T [S, N] (float64) and the scratch is the library's fixed array."""
     src = torch.as_tensor(src, dtype=torch.int32).contiguous().cpu()
+    _check_state_args(dgrid, s, int(src.numel()), out)
     cyc = C.c_int(0)
     _check(lib().eik_forward_noalloc(C.byref(dgrid.c), _dev(s, torch.float64, "s"), int(src.numel()),
                                      C.c_void_p(src.data_ptr()), _dev(out, torch.float64, "T"),
@@ -260,13 +277,17 @@ class Tangent:
                                    _stream()))
         return dT_full, d_rec
 
-    def apply_T(self, y: torch.Tensor, sum_sources: bool = True, g=None, lam_full=None):
-        """J^T y: y [S, n_rec, R]; returns (g, lam_full)."""
+    def apply_T(self, y: torch.Tensor, sum_sources: bool = True, g=None, lam_full=None, accumulate: bool = False):
+        """J^T y: y [S, n_rec, R]; returns (g, lam_full).  With accumulate (and
+        sum_sources) the source sum is added to the given g instead of replacing it."""
         R = y.shape[-1]
+        if accumulate and (g is None or not sum_sources):
+            raise ValueError("accumulate needs sum_sources and an existing g")
         if g is None:
             shape = (self.N, R) if sum_sources else (self.S, self.N, R)
             g = torch.empty(shape, dtype=y.dtype, device=y.device)
-        _check(lib().tangent_apply_T(self.h, _dev(y, name="y"), R, int(sum_sources), _dev(g, y.dtype, "g"),
+        mode = 2 if accumulate else int(bool(sum_sources))
+        _check(lib().tangent_apply_T(self.h, _dev(y, name="y"), R, mode, _dev(g, y.dtype, "g"),
                                      _dev(lam_full, y.dtype, "lam_full") if lam_full is not None else None,
                                      _dt(y.dtype), _stream()))
         return g, lam_full
@@ -433,10 +454,11 @@ class GN:
         _check(lib().gn_apply_T(self.h, _dev(y, self.dtype, "y"), _dev(out, self.dtype, "out"), _stream()))
         return out
 
-    def rhs(self, r: torch.Tensor, wd: torch.Tensor) -> torch.Tensor:
-        """b = [-W_d r; 0; 0] of Eq. (augmented-ls) for a residual r [S, n_rec]."""
-        b = torch.zeros(self.n_rows, dtype=self.dtype, device="cuda")
-        b[:self.n_data] = (-(wd * r)).reshape(-1).to(self.dtype)
+    def rhs(self, r: torch.Tensor) -> torch.Tensor:
+        """b = [-W_d r; 0; 0] of Eq. (augmented-ls) for a residual r [S, n_rec] (FP64),
+        formed on the device with the solver's own copy of W_d."""
+        b = torch.empty(self.n_rows, dtype=self.dtype, device="cuda")
+        _check(lib().gn_rhs(self.h, _dev(r.contiguous(), torch.float64, "r"), _dev(b, self.dtype, "b"), _stream()))
         return b
 
     def start(self, b: torch.Tensor):
