@@ -442,7 +442,7 @@ def run_gn(args):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         gn = eik.GN(tan, wd, vmodel, 0.01, 0.1, dtype=dtype, cells=args.cells)
-        b = gn.rhs(r, wd)
+        b = gn.rhs(r)
         gn.start(b)
         gn.iterate(1, use_graph=True)           # capture + first replay
         gn.start(b)

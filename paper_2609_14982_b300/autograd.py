@@ -57,16 +57,16 @@ class SlownessToTraveltime(torch.autograd.Function):
             ctx.tan.free()
             ctx.tan = None
             return g[:, 0], None, None, None, None, None
-        # recompute the frozen state chunk by chunk and accumulate the source sum
-        total = torch.zeros(ctx.dgrid.N, dtype=torch.float64, device=s.device)
+        # recompute the frozen state chunk by chunk; each chunk's source sum is added to
+        # the gradient by the library (tangent_apply_T with sum_sources = 2)
+        total = torch.zeros((ctx.dgrid.N, 1), dtype=torch.float64, device=s.device)
         for c0 in range(0, len(ctx.src), ctx.chunk):
             part = ctx.src[c0:c0 + ctx.chunk]
             T, _ = eik.eik_forward(ctx.dgrid, s, part, ctx.opts)
             tan = eik.Tangent(ctx.dgrid, T, s, part, rec=ctx.rec, opts=ctx.opts)
-            g, _ = tan.apply_T(y[c0:c0 + ctx.chunk].contiguous(), sum_sources=True)
-            total += g[:, 0]
+            tan.apply_T(y[c0:c0 + ctx.chunk].contiguous(), sum_sources=True, g=total, accumulate=True)
             tan.free()
-        return total, None, None, None, None, None
+        return total[:, 0], None, None, None, None, None
 
 
 def slowness_to_traveltime(s: torch.Tensor, dgrid, src, rec, opts=None, budget_bytes: int | None = None):

@@ -94,6 +94,7 @@ int tangent_apply_T(eik_tangent *t, const void *y, int R, int sum_sources, void 
     EIK_GUARD({
         if (!t) { eik::set_error("tangent is NULL"); return EIK_ERR_INVALID; }
         if (t->impl->n_rec == 0) { eik::set_error("tangent has no receivers"); return EIK_ERR_INVALID; }
+        if (sum_sources < 0 || sum_sources > 2) { eik::set_error("sum_sources must be 0, 1 or 2"); return EIK_ERR_INVALID; }
         return eik::traverse(t->impl, true, eik::MODE_J, y, 0, R, lam_full, g, sum_sources, dtype,
                              (cudaStream_t)stream);
     })

@@ -1386,7 +1386,7 @@ constexpr int SUMB = 8;
 
 template <typename T>
 __global__ void k_source_sum(long long N, int S, int R, const T *__restrict__ cqn, const int *__restrict__ pos,
-                             const T *__restrict__ lam, long long ld_lam, T *__restrict__ g, long long ld_g)
+                             const T *__restrict__ lam, long long ld_lam, T *__restrict__ g, long long ld_g, int accumulate)
 {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= N * R) return;
@@ -1412,7 +1412,7 @@ __global__ void k_source_sum(long long N, int S, int R, const T *__restrict__ cq
             }
         }
     }
-    g[j * ld_g + r] = acc;
+    g[j * ld_g + r] = accumulate ? g[j * ld_g + r] + acc : acc;
 }
 
 // Vector form of the same sum (same operations per element, in the same source order):
@@ -1427,7 +1427,7 @@ template <typename T, int V>
 __global__ void __launch_bounds__(256) k_source_sum_vec(long long N, int S, int R, int rows,
                                                         const T *__restrict__ cqn, const int *__restrict__ pos,
                                                         const T *__restrict__ lam, long long ld_lam, T *__restrict__ g,
-                                                        long long ld_g)
+                                                        long long ld_g, int accumulate)
 {
     using VT = typename VecT<T, V>::type;
     __shared__ int s_pos[SUM_STAGE * SUM_ROWS];
@@ -1481,7 +1481,14 @@ __global__ void __launch_bounds__(256) k_source_sum_vec(long long N, int S, int 
                 }
         }
     }
-    if (j < N) store<T, V>(g + j * ld_g + r, acc);
+    if (j < N) {
+        if (accumulate) {
+            const Pack<T, V> old = load_ro<T, V>(g + j * ld_g + r);
+#pragma unroll
+            for (int u = 0; u < V; ++u) acc.v[u] = old.v[u] + acc.v[u];
+        }
+        store<T, V>(g + j * ld_g + r, acc);
+    }
 }
 
 // receiver sampling P: out[a][k] = field[a][rec[a][k]]
@@ -1793,8 +1800,9 @@ static bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 // g[j][r] (row stride ld_g) = sum over sources of c_a[j] * x_a[j][r] for the w columns the
 // workspace holds (the reverse field of the last traversal, canonical order)
-int source_sum(Tangent *t, int w, void *g, long long ld_g, int dtype, cudaStream_t st)
+int source_sum(Tangent *t, int w, void *g, long long ld_g, int dtype, cudaStream_t st, bool accumulate)
 {
+    const int acc = accumulate ? 1 : 0;
     const void *xp = t->ws_vec;
     const int V = dtype == EIK_F32 ? 4 : 2;
     const int L = w / V;
@@ -1803,19 +1811,19 @@ int source_sum(Tangent *t, int w, void *g, long long ld_g, int dtype, cudaStream
         const unsigned blocks = (unsigned)((t->N + rows - 1) / rows);
         if (dtype == EIK_F32)
             k_source_sum_vec<float, 4><<<blocks, rows * L, 0, st>>>(t->N, t->S, w, rows, t->cqn32, t->pos,
-                                                                    (const float *)xp, (long long)w, (float *)g, ld_g);
+                                                                    (const float *)xp, (long long)w, (float *)g, ld_g, acc);
         else
             k_source_sum_vec<double, 2><<<blocks, rows * L, 0, st>>>(t->N, t->S, w, rows, t->cqn64, t->pos,
-                                                                     (const double *)xp, (long long)w, (double *)g, ld_g);
+                                                                     (const double *)xp, (long long)w, (double *)g, ld_g, acc);
     } else {
         const long long n = t->N * w;
         const unsigned blocks = (unsigned)((n + 255) / 256);
         if (dtype == EIK_F32)
             k_source_sum<float><<<blocks, 256, 0, st>>>(t->N, t->S, w, t->cqn32, t->pos, (const float *)xp, (long long)w,
-                                                        (float *)g, ld_g);
+                                                        (float *)g, ld_g, acc);
         else
             k_source_sum<double><<<blocks, 256, 0, st>>>(t->N, t->S, w, t->cqn64, t->pos, (const double *)xp, (long long)w,
-                                                         (double *)g, ld_g);
+                                                         (double *)g, ld_g, acc);
     }
     EIK_CHECK_LAUNCH();
     return EIK_OK;
@@ -1880,7 +1888,7 @@ int traverse(Tangent *t, bool TR, int mode, const void *in, int shared_in, int R
         else rc = TR ? dispatch_v<double, true>(t, P, st) : dispatch_v<double, false>(t, P, st);
         if (rc) return rc;
         if (TR && mode == MODE_J && sum_sources && out_aux) {
-            rc = source_sum(t, w, auxp, (long long)R, dtype, st);
+            rc = source_sum(t, w, auxp, (long long)R, dtype, st, sum_sources == 2);
             if (rc) return rc;
         }
     }

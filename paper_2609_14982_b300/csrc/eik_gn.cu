@@ -395,6 +395,16 @@ int lsmr_iteration(eik_gn *G, cudaStream_t st)
 
 }  // namespace
 
+// b = [-W_d r; 0; 0] (Eq. augmented-ls): -(w r) in FP64, then rounded to the vector type
+template <typename T>
+__global__ void k_gn_rhs(long long nd, long long n_rows, const double *__restrict__ wd, const double *__restrict__ r,
+                         T *__restrict__ b)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n_rows) return;
+    b[i] = i < nd ? (T)(-(wd[i] * r[i])) : T(0);
+}
+
 extern "C" {
 
 void gn_free(eik_gn *G)
@@ -507,6 +517,17 @@ int gn_apply_T(eik_gn *G, const void *y, void *out, eik_stream stream)
     cudaStream_t st = (cudaStream_t)stream;
     return G->dtype == EIK_F32 ? gn_transpose<float>(G, y, out, -1, nullptr, st)
                                : gn_transpose<double>(G, y, out, -1, nullptr, st);
+}
+
+int gn_rhs(eik_gn *G, const double *r, void *b, eik_stream stream)
+{
+    if (!G || !r || !b) { set_error("bad gn_rhs arguments"); return EIK_ERR_INVALID; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned blocks = (unsigned)((G->n_rows + 255) / 256);
+    if (G->dtype == EIK_F32) k_gn_rhs<float><<<blocks, 256, 0, st>>>(G->nd, G->n_rows, G->wd, r, (float *)b);
+    else k_gn_rhs<double><<<blocks, 256, 0, st>>>(G->nd, G->n_rows, G->wd, r, (double *)b);
+    EIK_CHECK_LAUNCH();
+    return EIK_OK;
 }
 
 int gn_lsmr_start(eik_gn *G, const void *b, eik_stream stream)

@@ -171,8 +171,9 @@ int sweep(Tangent *t, bool transpose, const void *b, int R, void *x, int dtype,
           const eik_opts *opts, int *cycles, cudaStream_t stream);
 
 int ensure_workspace(Tangent *t, size_t vec_bytes, size_t blk_elems);
-// g (row stride ld_g) = sum over sources of c_a x_a for the w columns in the workspace
-int source_sum(Tangent *t, int w, void *g, long long ld_g, int dtype, cudaStream_t st);
+// g (row stride ld_g) = sum over sources of c_a x_a for the w columns in the workspace, or
+// g += that sum when accumulate
+int source_sum(Tangent *t, int w, void *g, long long ld_g, int dtype, cudaStream_t st, bool accumulate = false);
 // off-grid receivers (multilinear P): set from host [S][n_rec][ndim] fractional indices,
 // then J p -> [S][n_rec][R] and J^T y -> [N][R] (summed over sources)
 // node <- cell averaging map (to_nodes) or its transpose, vectors [.][R]
