@@ -133,6 +133,20 @@ def graph_grid(n, A: float) -> Grid:
     return mapped_grid(tuple(n), (-L / 2, -L / 2), (L / 2, L / 2), H, zs)
 
 
+def closed_cycle_case(seed: int = 21):
+    """A frozen state whose dependency graph has a closed cyclic component: a seeded random
+    traveltime field (uniform noise plus a 0.3 depth trend) on a 9 x 9 grid sheared by
+    z_top = c x / 2 (c ~ U(0.5, 2) from the seed), unit slowness, source at node 0.  With
+    seed 21 one nontrivial SCC of 4 nodes has all its upwind faces inside itself, so its
+    rows of W sum to 1 and A_C = I - W_CC is singular, the case the local-invertibility
+    theorem of Sec. 4.2 excludes.  Returns (grid, T, s, src)."""
+    rng = np.random.default_rng(seed)
+    shear = rng.uniform(0.5, 2.0)
+    g = mapped_grid((9, 9), (0.0,), (8.0,), 8.0, lambda x: shear * x * 0.5)
+    T = rng.uniform(0, 1, g.N) + 0.3 * g.xyz[:, 1]
+    return g, T, np.ones(g.N), 0
+
+
 def quarter_source(g: Grid) -> int:
     """Surface node at logical (x, y) = (-L/4, -L/4)."""
     return g.index((g.n[0] - 1) // 4, (g.n[1] - 1) // 4, 0)

@@ -262,3 +262,30 @@ def test_state_converges_on_topography_3d(oracle_mod):
     s = 1.0 / W._velocity3d(g, 2.0)
     T, cyc = O.eik_forward(g, s, g.index(10, 10, 0))
     assert 0 < cyc < 100 and np.all(T >= 0) and np.isfinite(T).all()
+
+
+def test_closed_cycle_block_is_singular(oracle_mod):
+    """A state with a closed cyclic component (no upwind face leaves it): its rows of W
+    sum to 1, so A_C = I - W_CC has the all-ones null vector; the oracle's LU reports the
+    zero pivot and its tangent build refuses the state (Sec. 4.2, local invertibility)."""
+    import pytest
+    O = oracle_mod
+    g, T, s, src = W.closed_cycle_case()
+    _, G, _ = O.metric(g)
+    t = O.assemble(g, G, T, s, src)
+    lab = np.zeros(g.N, dtype=np.int32)
+    O.lib().or_scc(g.N, t.row_ptr, t.col, lab)
+    vals, counts = np.unique(lab, return_counts=True)
+    closed = []
+    for v, c in zip(vals, counts):
+        nodes = np.nonzero(lab == v)[0]
+        inside = set(nodes.tolist())
+        if c > 1 and all(int(t.col[e]) in inside for i in nodes for e in range(t.row_ptr[i], t.row_ptr[i + 1])):
+            closed.append(nodes)
+    assert len(closed) == 1 and len(closed[0]) == 4
+    Ac = O.block_matrix(t, closed[0])
+    assert np.max(np.abs(Ac @ np.ones(4))) <= 1e-15          # rows of W_CC sum to 1
+    piv = np.zeros(4, dtype=np.int32)
+    assert O.lib().or_lu(4, np.ascontiguousarray(Ac.reshape(-1)).copy(), piv) != 0
+    with pytest.raises(np.linalg.LinAlgError):
+        O.build_tangent(g, G, T, s, src)
