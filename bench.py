@@ -299,20 +299,31 @@ def run_ours(args):
                 "other_direction": {"dir": other, "ms": round(mb, 4), "includes": "k_source_sum_vec",
                                     "frac": round(ab[other] / (mb / 1e3) / 1e9 / peak, 4)}}
 
-    # ---- the plain form on the same B300: directional sweeping of the same operator
+    # ---- the plain form on the same B300: directional sweeping of the same operator, the
+    # same right-hand sides per source (R = 64, FP32), timed with CUDA events around whole
+    # solves (each cycle ends with the stopping test's device-to-host read)
     sweep = None
     if not args.no_sweep:
-        Rs = 8
-        q = torch.randn((S, N, Rs), device=dev, dtype=dtype, generator=gen)
-        so = eik.default_opts(sweep_tol=1e-6)
+        q = torch.randn((S, N, R), device=dev, dtype=dtype, generator=gen)
+        xs = torch.empty_like(q)
+        so = eik.default_opts(sweep_tol=args.sweep_tol)
+        tan.sweep(q, transpose=False, opts=so, out=xs)       # builds the slotted weights and the cycle graph
+        tan.sweep(q, transpose=True, opts=so, out=xs)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        _, c1 = tan.sweep(q, transpose=False, opts=so, out=xs)
+        ev[1].record(stream)
+        _, c2 = tan.sweep(q, transpose=True, opts=so, out=xs)
+        ev[2].record(stream)
         torch.cuda.synchronize()
-        t0 = time.time()
-        _, c1 = tan.sweep(q, transpose=False, opts=so)
-        _, c2 = tan.sweep(q, transpose=True, opts=so)
-        torch.cuda.synchronize()
-        ts = time.time() - t0
-        sweep = {"value": 2.0 * N * S * Rs / ts, "unit": UNIT, "cycles": [c1, c2], "R": Rs,
-                 "tol": 1e-6, "speedup_btf_over_sweep": round(value / (2.0 * N * S * Rs / ts), 1)}
+        tf, tb = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        sweep_value = 2.0 * N * S * R / ((tf + tb) / 1e3)
+        sweep = {"value": sweep_value, "unit": UNIT, "cycles": [c1, c2], "R": R, "tol": args.sweep_tol,
+                 "ms": [round(tf, 3), round(tb, 3)], "ms_per_cycle": [round(tf / c1, 3), round(tb / c2, 3)],
+                 "visits_per_update": (1 << g.ndim) * (c1 + c2) / 2.0,
+                 "speedup_btf_over_sweep": round(value / sweep_value, 1)}
+        del q, xs
+        torch.cuda.empty_cache()
 
     cpu = None if args.no_cpu else cpu_baseline(wl, args.cpu_sample_sources)
     out = {
@@ -720,6 +731,8 @@ def main():
     ap.add_argument("--level-waits", action="store_true",
                     help="persistent items wait for their whole previous level, not only their upstream items")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--sweep-tol", type=float, default=1e-6,
+                    help="sweeping baseline: stop at max |dx| <= tol max |x| over a cycle (FP32 path)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-sources", type=int, default=2)
     ap.add_argument("--sources", type=int, default=0, help="use only the first K sources (small profiling case)")

@@ -39,7 +39,8 @@ def _sources():
 
 def _digest() -> str:
     h = hashlib.sha256()
-    for f in _sources() + sorted(glob.glob(os.path.join(CSRC, "*.h"))) + [os.path.join(INCLUDE, "eik.h"), __file__]:
+    for f in _sources() + sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))) + \
+            [os.path.join(INCLUDE, "eik.h"), __file__]:
         h.update(open(f, "rb").read())
     return h.hexdigest()
 

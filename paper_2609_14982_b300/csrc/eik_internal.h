@@ -155,6 +155,11 @@ struct Tangent {
     std::map<long long, cudaGraphExec_t> level_graphs;
     cudaStream_t cap_stream = nullptr;
     bool opts_graph = true;
+    // directional sweeping (the plain form): slotted weights per (direction, precision),
+    // the stopping-test words and one captured cycle per (direction, precision, R, b, x)
+    void *sweep_w[4] = {nullptr, nullptr, nullptr, nullptr};
+    unsigned int *sweep_flags = nullptr;
+    std::map<std::vector<long long>, cudaGraphExec_t> sweep_graphs;
 };
 
 int build_tangent(const eik_grid *g, const double *T, const double *s, int S, const int *src_node,

@@ -825,6 +825,9 @@ void free_tangent(Tangent *t)
                     t->ws_in, t->lvl_d, t->blk_lvl_d, t->nlev_d, t->order_d};
     for (void *p : ptrs) if (p) cudaFree(p);
     if (t->params_d) cudaFree((void *)t->params_d);
+    for (void *p : t->sweep_w) if (p) cudaFree(p);
+    if (t->sweep_flags) cudaFree(t->sweep_flags);
+    for (auto &kv : t->sweep_graphs) if (kv.second) cudaGraphExecDestroy(kv.second);
     for (auto &kv : t->level_graphs) if (kv.second) cudaGraphExecDestroy(kv.second);
     if (t->cap_stream) cudaStreamDestroy(t->cap_stream);
     delete t;
