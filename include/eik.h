@@ -231,6 +231,25 @@ int tangent_apply_T(eik_tangent *t, const void *y, int R, int sum_sources,
                     void *g, void *lam_full, int dtype, eik_stream stream);
 
 /*
+ * tangent_apply_batch / tangent_apply_T_batch -- J p and J^T y (as tangent_apply with a
+ * shared model and tangent_apply_T with the source sum, Sec. 4.4) of up to 4 tangents,
+ * e.g. one per grid of a multi-grid workload, in ONE launch of the cluster schedule:
+ * thread-block clusters take (tangent, source) units from one queue (tangents in the
+ * order given, a tangent's sources by decreasing level count), so condensation DAGs of
+ * uneven depth and size run side by side.
+ *   t[k]      tangent k (same device for all)
+ *   p[k]      device [N_k][R[k]] model vector block of tangent k (shared by its sources)
+ *   y[k]      device [S_k][n_rec_k][R[k]] receiver data
+ *   d_rec[k]  device [S_k][n_rec_k][R[k]] output;  g[k] device [N_k][R[k]] output
+ *   dtype     common to all; R[k] may differ (the widest vector dividing all is used)
+ * Every tangent's internal workspace is sized to all R[k] columns (no column chunks).
+ */
+int tangent_apply_batch(eik_tangent *const *t, int ntan, const void *const *p, const int *R, void *const *d_rec,
+                        int dtype, eik_stream stream);
+int tangent_apply_T_batch(eik_tangent *const *t, int ntan, const void *const *y, const int *R, void *const *g,
+                          int dtype, eik_stream stream);
+
+/*
  * tangent_solve / tangent_solve_T -- the bare transport solves dT = A^-1 q and
  * lam = A^-T r for all sources (Prop. 3, Sec. 4.3), q and r device [S][N][R],
  * outputs device [S][N][R].  Used for parity tests of the traversal alone.

@@ -100,6 +100,32 @@ int tangent_apply_T(eik_tangent *t, const void *y, int R, int sum_sources, void 
     })
 }
 
+static int batch_entry(eik_tangent *const *t, int ntan, bool tr, const void *const *in, const int *R,
+                       void *const *out, int dtype, eik_stream stream)
+{
+    EIK_GUARD({
+        if (!t || !in || !R || !out || ntan < 1 || ntan > 4) { eik::set_error("bad batch arguments"); return EIK_ERR_INVALID; }
+        Tangent *ts[4];
+        for (int k = 0; k < ntan; ++k) {
+            if (!t[k]) { eik::set_error("batch: tangent %d is NULL", k); return EIK_ERR_INVALID; }
+            ts[k] = t[k]->impl;
+        }
+        return eik::traverse_batch(ts, ntan, tr, in, R, out, dtype, (cudaStream_t)stream);
+    })
+}
+
+int tangent_apply_batch(eik_tangent *const *t, int ntan, const void *const *p, const int *R, void *const *d_rec,
+                        int dtype, eik_stream stream)
+{
+    return batch_entry(t, ntan, false, p, R, d_rec, dtype, stream);
+}
+
+int tangent_apply_T_batch(eik_tangent *const *t, int ntan, const void *const *y, const int *R, void *const *g,
+                          int dtype, eik_stream stream)
+{
+    return batch_entry(t, ntan, true, y, R, g, dtype, stream);
+}
+
 int tangent_set_receivers(eik_tangent *t, int n_rec, const double *f)
 {
     EIK_GUARD({

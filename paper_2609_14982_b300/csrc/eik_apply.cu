@@ -1789,6 +1789,41 @@ int source_sum(Tangent *t, int w, void *g, long long ld_g, int dtype, cudaStream
     return EIK_OK;
 }
 
+// launch parameters of one traversal call (a column chunk of w right-hand sides starting
+// at the given input/output pointers; row strides R)
+static TravParams make_params(Tangent *t, bool TR, int mode, const void *inp, int shared_in, int w, int R, void *xp,
+                              void *outp, void *auxp, int sum_sources, int dtype)
+{
+    TravParams P{};
+    P.S = t->S; P.R = w; P.n_rec = t->n_rec; P.maxL = t->maxL; P.nitems = t->nitems; P.N = t->N;
+    P.item_max = t->item_max;
+    P.ld_in = R; P.ld_x = w; P.ld_aux = R; P.ld_out = R;
+    P.out = outp;
+    P.mode = mode; P.shared_in = shared_in; P.sum = sum_sources;
+    P.perm = t->perm;
+    P.rowptr = TR ? t->cptr : t->rowptr;
+    P.enode = TR ? t->dn_node : t->up_node;
+    P.ew = dtype == EIK_F32 ? (const void *)(TR ? t->dn_w32 : t->up_w32) : (const void *)(TR ? t->dn_w64 : t->up_w64);
+    P.ew64 = TR ? t->dn_w64 : t->up_w64;
+    P.ebase = TR ? t->tbase_d : t->ebase_d;
+    P.cq = dtype == EIK_F32 ? (const void *)t->cq32 : (const void *)t->cq64;
+    P.cq64 = t->cq64;
+    P.rec_slot = t->rec_slot;
+    P.in = inp; P.x = xp; P.aux = auxp;
+    P.items = TR ? t->items_bwd : t->items_fwd;
+    P.ebeg = TR ? t->ebeg_bwd : t->ebeg_fwd;
+    P.item_cnt = t->item_cnt + (TR ? (size_t)t->S * t->maxL : 0);
+    P.done = t->done; P.ticket = t->ticket; P.err = t->err;
+    P.deps = TR ? t->deps_bwd : t->deps_fwd;
+    // while a test hold is in place every item takes the level wait it targets
+    P.ndeps = t->opts.item_deps && t->holds.empty() ? (TR ? t->ndeps_bwd : t->ndeps_fwd) : nullptr;
+    P.item_done = t->item_done;
+    P.blk_desc = t->blk_desc; P.blk_off = t->blk_off; P.binv = t->binv; P.ws = t->ws_blk;
+    P.timeout_ns = (unsigned long long)(t->opts.wait_timeout_s * 1e9);
+    P.lvl = t->lvl_d; P.blk_lvl = t->blk_lvl_d; P.nlev = t->nlev_d; P.order = t->order_d;
+    return P;
+}
+
 int traverse(Tangent *t, bool TR, int mode, const void *in, int shared_in, int R, void *out_full, void *out_aux,
              int sum_sources, int dtype, cudaStream_t st)
 {
@@ -1817,33 +1852,7 @@ int traverse(Tangent *t, bool TR, int mode, const void *in, int shared_in, int R
         char *xp = static_cast<char *>(t->ws_vec);
         char *outp = out_full ? static_cast<char *>(out_full) + r0 * esz : nullptr;
         char *auxp = out_aux ? static_cast<char *>(out_aux) + r0 * esz : nullptr;
-        TravParams P{};
-        P.S = t->S; P.R = w; P.n_rec = t->n_rec; P.maxL = t->maxL; P.nitems = t->nitems; P.N = t->N;
-        P.item_max = t->item_max;
-        P.ld_in = R; P.ld_x = w; P.ld_aux = R; P.ld_out = R;
-        P.out = outp;
-        P.mode = mode; P.shared_in = shared_in; P.sum = sum_sources;
-        P.perm = t->perm;
-        P.rowptr = TR ? t->cptr : t->rowptr;
-        P.enode = TR ? t->dn_node : t->up_node;
-        P.ew = dtype == EIK_F32 ? (const void *)(TR ? t->dn_w32 : t->up_w32) : (const void *)(TR ? t->dn_w64 : t->up_w64);
-        P.ew64 = TR ? t->dn_w64 : t->up_w64;
-        P.ebase = TR ? t->tbase_d : t->ebase_d;
-        P.cq = dtype == EIK_F32 ? (const void *)t->cq32 : (const void *)t->cq64;
-        P.cq64 = t->cq64;
-        P.rec_slot = t->rec_slot;
-        P.in = inp; P.x = xp; P.aux = auxp;
-        P.items = TR ? t->items_bwd : t->items_fwd;
-        P.ebeg = TR ? t->ebeg_bwd : t->ebeg_fwd;
-        P.item_cnt = t->item_cnt + (TR ? (size_t)t->S * t->maxL : 0);
-        P.done = t->done; P.ticket = t->ticket; P.err = t->err;
-        P.deps = TR ? t->deps_bwd : t->deps_fwd;
-        // while a test hold is in place every item takes the level wait it targets
-        P.ndeps = t->opts.item_deps && t->holds.empty() ? (TR ? t->ndeps_bwd : t->ndeps_fwd) : nullptr;
-        P.item_done = t->item_done;
-        P.blk_desc = t->blk_desc; P.blk_off = t->blk_off; P.binv = t->binv; P.ws = t->ws_blk;
-        P.timeout_ns = (unsigned long long)(t->opts.wait_timeout_s * 1e9);
-        P.lvl = t->lvl_d; P.blk_lvl = t->blk_lvl_d; P.nlev = t->nlev_d; P.order = t->order_d;
+        TravParams P = make_params(t, TR, mode, inp, shared_in, w, R, xp, outp, auxp, sum_sources, dtype);
         if (dtype == EIK_F32) rc = TR ? dispatch_v<float, true>(t, P, st) : dispatch_v<float, false>(t, P, st);
         else rc = TR ? dispatch_v<double, true>(t, P, st) : dispatch_v<double, false>(t, P, st);
         if (rc) return rc;
@@ -1852,6 +1861,81 @@ int traverse(Tangent *t, bool TR, int mode, const void *in, int shared_in, int R
             if (rc) return rc;
         }
     }
+    return EIK_OK;
+}
+
+// ---------------------------------------------------------------- batched tangents
+template <typename T, int V, bool TR>
+static int launch_batch(Tangent *const *ts, int ntan, const TravParams *Ps, const int *R, cudaStream_t st)
+{
+    Tangent *t0 = ts[0];
+    ClusterBatch B{};
+    B.ntan = ntan;
+    B.unit_ptr[0] = 0;
+    int min_lanes = 1 << 30, W = 4, tab = 0;
+    for (int k = 0; k < ntan; ++k) {
+        B.P[k] = Ps[k];
+        B.unit_ptr[k + 1] = B.unit_ptr[k] + ts[k]->S;
+        B.lanes[k] = R[k] / V;
+        min_lanes = std::min(min_lanes, B.lanes[k]);
+        if (B.lanes[k] % 4) W = std::min(W, B.lanes[k] % 2 ? 1 : 2);
+        tab = std::max(tab, ts[k]->maxL + 1);
+    }
+    const int cap = t0->opts.pass_units > 0 ? t0->opts.pass_units : 4;
+    W = std::min(W, cap >= 4 ? 4 : (cap >= 2 ? 2 : 1));
+    const int threads = t0->opts.cluster_threads > 0 ? t0->opts.cluster_threads : 256;
+    for (int k = 0; k < ntan; ++k)
+        if (B.lanes[k] / W > threads) {
+            set_error("batch: %d right-hand-side lanes exceed %d threads per CTA", B.lanes[k], threads);
+            return EIK_ERR_INVALID;
+        }
+    B.tp = std::min(512, (4 / W) * (threads / std::max(1, min_lanes / W)));
+    B.tab = tab;
+    while (B.tp > 32 && CL_SLOTS * cl_slot_bytes<T>(B.tp) + 3 * (size_t)B.tab * sizeof(int) > 160 * 1024) B.tp /= 2;
+    B.ticket = t0->ticket + 1;
+    const int units = B.unit_ptr[ntan];
+    if (W == 4) return launch_cluster_u<T, V, TR, 4>(t0, B, units, st);
+    if (W == 2) return launch_cluster_u<T, V, TR, 2>(t0, B, units, st);
+    return launch_cluster_u<T, V, TR, 1>(t0, B, units, st);
+}
+
+int traverse_batch(Tangent *const *ts, int ntan, bool TR, const void *const *in, const int *R, void *const *out,
+                   int dtype, cudaStream_t st)
+{
+    if (ntan < 1 || ntan > CL_MAXTAN) { set_error("batch: 1..%d tangents", CL_MAXTAN); return EIK_ERR_INVALID; }
+    if (dtype != EIK_F32 && dtype != EIK_F64) { set_error("bad dtype"); return EIK_ERR_INVALID; }
+    const size_t esz = dtype == EIK_F32 ? 4 : 8;
+    TravParams Ps[CL_MAXTAN];
+    int V = dtype == EIK_F32 ? 4 : 2;
+    for (int k = 0; k < ntan; ++k) {
+        Tangent *t = ts[k];
+        if (!t || !in[k] || !out[k] || R[k] <= 0) { set_error("batch: bad arguments of tangent %d", k); return EIK_ERR_INVALID; }
+        if (t->n_rec == 0) { set_error("batch: tangent %d has no receivers", k); return EIK_ERR_INVALID; }
+        if (!aligned16(in[k]) || !aligned16(out[k])) { set_error("device buffers must be 16-byte aligned"); return EIK_ERR_INVALID; }
+        if (t->device != ts[0]->device) { set_error("batch: tangents on different devices"); return EIK_ERR_INVALID; }
+        while (R[k] % V) V >>= 1;
+        // every right-hand side of every tangent in one pass: the workspace holds them all
+        int rc = ensure_workspace(t, (size_t)t->S * t->N * R[k] * esz, (size_t)t->ws_rows * R[k]);
+        if (rc) return rc;
+    }
+    for (int k = 0; k < ntan; ++k)
+        Ps[k] = make_params(ts[k], TR, MODE_J, in[k], TR ? 0 : 1, R[k], R[k], ts[k]->ws_vec, nullptr,
+                            TR ? nullptr : out[k], TR ? 1 : 0, dtype);
+    int rc;
+    if (dtype == EIK_F32) {
+        if (V == 4) rc = TR ? launch_batch<float, 4, true>(ts, ntan, Ps, R, st) : launch_batch<float, 4, false>(ts, ntan, Ps, R, st);
+        else if (V == 2) rc = TR ? launch_batch<float, 2, true>(ts, ntan, Ps, R, st) : launch_batch<float, 2, false>(ts, ntan, Ps, R, st);
+        else rc = TR ? launch_batch<float, 1, true>(ts, ntan, Ps, R, st) : launch_batch<float, 1, false>(ts, ntan, Ps, R, st);
+    } else {
+        if (V == 2) rc = TR ? launch_batch<double, 2, true>(ts, ntan, Ps, R, st) : launch_batch<double, 2, false>(ts, ntan, Ps, R, st);
+        else rc = TR ? launch_batch<double, 1, true>(ts, ntan, Ps, R, st) : launch_batch<double, 1, false>(ts, ntan, Ps, R, st);
+    }
+    if (rc) return rc;
+    if (TR)
+        for (int k = 0; k < ntan; ++k) {
+            rc = source_sum(ts[k], R[k], out[k], (long long)R[k], dtype, st);
+            if (rc) return rc;
+        }
     return EIK_OK;
 }
 

@@ -172,6 +172,11 @@ enum Mode : int { MODE_J = 0, MODE_RAW = 1 };
 int traverse(Tangent *t, bool transpose, int mode, const void *in, int shared_in, int R,
              void *out_full, void *out_aux, int sum_sources, int dtype, cudaStream_t stream);
 
+// J p (TR false: in = shared model p [N_k][R_k], out = d_rec) or J^T y summed over
+// sources (TR true: in = y, out = g [N_k][R_k]) of several tangents in one cluster launch
+int traverse_batch(Tangent *const *ts, int ntan, bool TR, const void *const *in, const int *R, void *const *out,
+                   int dtype, cudaStream_t st);
+
 int sweep(Tangent *t, bool transpose, const void *b, int R, void *x, int dtype,
           const eik_opts *opts, int *cycles, cudaStream_t stream);
 

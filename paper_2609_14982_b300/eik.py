@@ -28,7 +28,8 @@ EXPORTED = ["eik_opts_default", "eik_last_error", "eik_version", "eik_forward", 
             "eik_forward_noalloc", "eik_forward_noalloc_capacity",
             "gn_create", "gn_dims", "gn_apply", "gn_apply_T", "gn_lsmr_start", "gn_lsmr_iterate",
             "gn_lsmr_solution", "gn_free", "model_cells_to_nodes", "model_nodes_to_cells",
-            "tangent_set_receivers", "tangent_apply_interp", "tangent_apply_interp_T", "gn_create_cells", "gn_rhs"]
+            "tangent_set_receivers", "tangent_apply_interp", "tangent_apply_interp_T", "gn_create_cells", "gn_rhs",
+            "tangent_apply_batch", "tangent_apply_T_batch"]
 
 
 class EikError(RuntimeError):
@@ -102,6 +103,8 @@ def lib():
         L.gn_apply_T.argtypes = [P, P, P, P]
         L.gn_lsmr_start.argtypes = [P, P, P]
         L.gn_rhs.argtypes = [P, P, P, P]
+        L.tangent_apply_batch.argtypes = [P, I, P, P, P, I, P]
+        L.tangent_apply_T_batch.argtypes = [P, I, P, P, P, I, P]
         L.gn_lsmr_iterate.argtypes = [P, I, I, P]
         L.gn_lsmr_solution.argtypes = [P, P, P, P]
         L.gn_free.argtypes = [P]
@@ -383,6 +386,33 @@ class Tangent:
         _check(lib().tangent_export(self.h, a, *ptrs))
         return dict(label=label, level=level, perm=perm, level_ptr=level_ptr, row_ptr=row_ptr,
                     col=col[:st["edges"]], w=w[:st["edges"]], cs=cs, stats=st)
+
+
+def _batch(fn, tans, xs, outs):
+    n = len(tans)
+    if not 1 <= n <= 4 or len(xs) != n or len(outs) != n:
+        raise ValueError("a batch holds 1..4 tangents with one input and one output each")
+    dtype = xs[0].dtype
+    th = (C.c_void_p * n)(*[t.h.value for t in tans])
+    xp = (C.c_void_p * n)(*[_dev(x, dtype, "input") for x in xs])
+    op = (C.c_void_p * n)(*[_dev(o, dtype, "output") for o in outs])
+    rr = (C.c_int * n)(*[int(x.shape[-1]) for x in xs])
+    _check(fn(th, n, xp, rr, op, _dt(dtype), _stream()))
+    return outs
+
+
+def apply_batch(tans, ps):
+    """J p of several tangents (e.g. one per grid) in one launch: ps[k] [N_k, R_k] shared
+    model blocks; returns the d_rec [S_k, n_rec_k, R_k] of each."""
+    outs = [torch.empty((t.S, t.n_rec, p.shape[-1]), dtype=p.dtype, device=p.device) for t, p in zip(tans, ps)]
+    return _batch(lib().tangent_apply_batch, tans, ps, outs)
+
+
+def apply_T_batch(tans, ys):
+    """J^T y summed over sources for several tangents in one launch: ys[k]
+    [S_k, n_rec_k, R_k]; returns the g [N_k, R_k] of each."""
+    outs = [torch.empty((t.N, y.shape[-1]), dtype=y.dtype, device=y.device) for t, y in zip(tans, ys)]
+    return _batch(lib().tangent_apply_T_batch, tans, ys, outs)
 
 
 class LSQR:
