@@ -5,9 +5,13 @@
 // coefficient a_f decides whether an edge exists, and it must come out of the same
 // sequence of correctly rounded IEEE operations that the formulas below state.
 #include <cub/cub.cuh>
+#include <thrust/iterator/counting_iterator.h>
 
 #include <algorithm>
+#include <atomic>
+#include <climits>
 #include <cstdarg>
+#include <thread>
 #include <cstdio>
 #include <cstring>
 
@@ -230,106 +234,86 @@ __device__ __forceinline__ void for_succs(const GridDesc &g, long long v, const 
         }
 }
 
-// Kahn rounds (Sec. 3.5): fst[v] = first round in which every predecessor of v was
-// already removed.  A predecessor stamped in the current round does not count, so the
-// result does not depend on thread order.
-__global__ void k_fwd_trim(GridDesc g, long long SN, const unsigned char *__restrict__ upmask, int *fst, int t,
-                           int *changed)
+// ---------------------------------------------------------------------------
+// Kahn trimming with frontier queues (Sec. 3.5, Prop. 2): each round removes the
+// vertices whose last remaining predecessor (successor) was removed in the previous
+// round, so the total work is O(V + E) instead of one pass over all vertices per round.
+// fst[v] = Kahn round of v = 1 + max over predecessors (0 without predecessor), INF for
+// the downstream closure of the cycles; bst likewise from the sinks of that residual.
+// The values do not depend on the order inside a frontier.
+// ---------------------------------------------------------------------------
+__global__ void k_trim_fwd_init(long long SN, const unsigned char *__restrict__ upmask, int *deg, int *fst, int *front,
+                                int *nfront)
 {
-    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (v >= SN || fst[v] != INF) return;
-    bool ready = true;
-    for_preds(g, v, upmask[v], [&](long long u) { if (fst[u] >= t) ready = false; });
-    if (ready) { fst[v] = t; *changed = 1; }
-}
-
-// backward trimming of the Kahn residual: remove vertices none of whose successors
-// inside the residual remains
-__global__ void k_bwd_trim(GridDesc g, long long SN, const unsigned char *__restrict__ upmask,
-                           const int *__restrict__ fst, int *bst, int t, int *changed)
-{
-    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (v >= SN || fst[v] != INF || bst[v] != INF) return;
-    bool ready = true;
-    for_succs(g, v, upmask, [&](long long u) { if (fst[u] == INF && bst[u] >= t) ready = false; });
-    if (ready) { bst[v] = t; *changed = 1; }
-}
-
-__global__ void k_collect(long long SN, const int *__restrict__ fst, const int *__restrict__ bst, int *list, int *count,
-                          int *label, int *act)
-{
-    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (v >= SN) return;
-    if (fst[v] == INF && bst[v] == INF) {
-        int k = atomicAdd(count, 1);
-        list[k] = (int)v;
-        act[v] = 1;
-        label[v] = -1;
-    } else {
-        act[v] = 0;
-        label[v] = (int)v;
+    const int d = __popc((unsigned)upmask[v]);
+    deg[v] = d;
+    fst[v] = INF;
+    if (d == 0) { fst[v] = 0; front[atomicAdd(nfront, 1)] = (int)v; }
+}
+
+__global__ void k_trim_fwd_step(GridDesc g, const unsigned char *__restrict__ upmask, int *deg, int *fst,
+                                const int *__restrict__ cur, const int *ncur, int *next, int *nnext, int round)
+{
+    const int n = *ncur;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const long long v = cur[k];
+        for_succs(g, v, upmask, [&](long long u) {
+            if (atomicSub(&deg[u], 1) == 1) { fst[u] = round + 1; next[atomicAdd(nnext, 1)] = (int)u; }
+        });
     }
 }
 
-// Colouring SCC (forward min-label propagation + backward closure from the roots):
-// colour[v] = smallest active vertex that reaches v; the vertices with the root's
-// colour that reach the root form the root's SCC, whose smallest vertex is the root.
-__global__ void k_color_init(const int *list, int n, const int *act, int *color, int *inscc)
+__global__ void k_trim_bwd_init(GridDesc g, long long SN, const unsigned char *__restrict__ upmask,
+                                const int *__restrict__ fst, int *deg, int *bst, int *front, int *nfront)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    int v = list[k];
-    if (!act[v]) return;
-    color[v] = v;
-    inscc[v] = 0;
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= SN) return;
+    bst[v] = INF;
+    if (fst[v] != INF) return;
+    int d = 0;
+    for_succs(g, v, upmask, [&](long long u) { if (fst[u] == INF) ++d; });
+    deg[v] = d;
+    if (d == 0) { bst[v] = 0; front[atomicAdd(nfront, 1)] = (int)v; }
 }
 
-__global__ void k_color_prop(GridDesc g, const int *list, int n, const unsigned char *__restrict__ upmask,
-                             const int *act, int *color, int *changed)
+__global__ void k_trim_bwd_step(GridDesc g, const unsigned char *__restrict__ upmask, const int *__restrict__ fst,
+                                int *deg, int *bst, const int *__restrict__ cur, const int *ncur, int *next, int *nnext,
+                                int round)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    int v = list[k];
-    if (!act[v]) return;
-    int m = color[v];
-    for_preds(g, v, upmask[v], [&](long long u) {
-        if (act[u]) { int cu = *(volatile int *)&color[u]; if (cu < m) m = cu; }
-    });
-    if (m < color[v]) { atomicMin(&color[v], m); *changed = 1; }
+    const int n = *ncur;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const long long v = cur[k];
+        for_preds(g, v, upmask[v], [&](long long u) {
+            if (fst[u] == INF && atomicSub(&deg[u], 1) == 1) { bst[u] = round + 1; next[atomicAdd(nnext, 1)] = (int)u; }
+        });
+    }
 }
 
-__global__ void k_scc_roots(const int *list, int n, const int *act, const int *color, int *inscc)
+// residual flag (in both closures: downstream and upstream of a cycle) and labels of
+// every vertex outside it (singleton components: the vertex itself)
+__global__ void k_residual_flags(long long SN, const int *__restrict__ fst, const int *__restrict__ bst,
+                                 unsigned char *flag, int *label)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    int v = list[k];
-    if (act[v] && color[v] == v) inscc[v] = 1;
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= SN) return;
+    const bool r = fst[v] == INF && bst[v] == INF;
+    flag[v] = r;
+    label[v] = (int)v;
 }
 
-__global__ void k_scc_back(GridDesc g, const int *list, int n, const unsigned char *__restrict__ upmask, const int *act,
-                           const int *color, int *inscc, int *changed)
+__global__ void k_gather_masks(const int *__restrict__ list, int n, const unsigned char *__restrict__ upmask,
+                               unsigned char *out)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    int v = list[k];
-    if (!act[v] || inscc[v]) return;
-    bool hit = false;
-    int cv = color[v];
-    for_succs(g, v, upmask, [&](long long u) {
-        if (act[u] && color[u] == cv && *(volatile int *)&inscc[u]) hit = true;
-    });
-    if (hit) { inscc[v] = 1; *changed = 1; }
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = upmask[list[k]];
 }
 
-__global__ void k_scc_take(const int *list, int n, int *act, const int *color, const int *inscc, int *label,
-                           int *remaining)
+__global__ void k_scatter_labels(const int *__restrict__ list, const int *__restrict__ lab_res, int n, int *label)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    int v = list[k];
-    if (!act[v]) return;
-    if (inscc[v]) { label[v] = color[v]; act[v] = 0; }
-    else atomicAdd(remaining, 1);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) label[list[k]] = lab_res[k];
 }
 
 __global__ void k_comp_size(long long SN, const int *__restrict__ label, int *csize)
@@ -639,12 +623,6 @@ __global__ void k_block_lu(const int4 *__restrict__ desc, const long long *__res
     }
 }
 
-__global__ void k_fill_inf(long long n, int *p)
-{
-    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (v < n) p[v] = INF;
-}
-
 __global__ void k_check_assigned(long long SN, const int *label, const int *asg, int *bad)
 {
     long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -811,6 +789,66 @@ cudaError_t dalloc(T **p, size_t n) { return cudaMalloc((void **)p, std::max<siz
 
 inline unsigned blocks_for(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// Tarjan's algorithm (Sec. 4.1 [ref50]), iterative, on the residual vertices of one
+// source: `nodes` ascending (global indices), `masks` their upwind-face bits; the edges
+// are the upwind faces whose neighbour is also residual.  Writes for every vertex the
+// smallest global index of its strongly connected component (the canonical label).
+void tarjan_residual(const GridDesc &g, const int *nodes, const unsigned char *masks, int n, int *out)
+{
+    std::vector<int> index(n, -1), low(n), stk;
+    std::vector<char> on(n, 0);
+    struct Frame { int v; int b; };
+    std::vector<Frame> cs;
+    int counter = 0;
+    auto find = [&](long long u) -> int {
+        const int *it = std::lower_bound(nodes, nodes + n, (int)u);
+        return (it != nodes + n && *it == u) ? (int)(it - nodes) : -1;
+    };
+    for (int r = 0; r < n; ++r) {
+        if (index[r] >= 0) continue;
+        index[r] = low[r] = counter++;
+        stk.push_back(r);
+        on[r] = 1;
+        cs.push_back({r, 0});
+        while (!cs.empty()) {
+            const int v = cs.back().v;
+            int w = -1;
+            while (cs.back().b < 2 * g.ndim) {
+                const int b = cs.back().b++;
+                if (!(masks[v] & (1u << b))) continue;
+                const int d = b >> 1, side = (b & 1) ? 1 : -1;
+                const int u = find((long long)nodes[v] + side * g.st[d]);
+                if (u < 0) continue;
+                if (index[u] < 0) { w = u; break; }
+                if (on[u]) low[v] = std::min(low[v], index[u]);
+            }
+            if (w >= 0) {   // descend
+                index[w] = low[w] = counter++;
+                stk.push_back(w);
+                on[w] = 1;
+                cs.push_back({w, 0});
+                continue;
+            }
+            if (low[v] == index[v]) {   // v roots a component: pop it
+                int m = nodes[v];
+                for (size_t k = stk.size(); k-- > 0;) {
+                    m = std::min(m, nodes[stk[k]]);
+                    if (stk[k] == v) break;
+                }
+                for (;;) {
+                    const int x = stk.back();
+                    stk.pop_back();
+                    on[x] = 0;
+                    out[x] = m;
+                    if (x == v) break;
+                }
+            }
+            cs.pop_back();
+            if (!cs.empty()) { const int p = cs.back().v; low[p] = std::min(low[p], low[v]); }
+        }
+    }
+}
+
 }  // namespace
 
 void free_tangent(Tangent *t)
@@ -853,7 +891,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
 
     Scratch sc;
     double *G, *gT;
-    int *cnt, *fst, *bst, *flags, *src_d, *lab, *act, *color, *inscc, *list, *csize, *lvl, *asg, *cmax, *blk, *lmax;
+    int *cnt, *fst, *bst, *flags, *src_d, *lab, *act, *color, *list, *csize, *lvl, *asg, *cmax, *blk, *lmax;
     unsigned char *upmask;
     unsigned long long *nid;
     TRY(sc.get(&G, N * nd * nd));
@@ -882,69 +920,103 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
                                                t->cs_nat, nid);
     TRY(cudaGetLastError());
 
-    // ---- forward and backward trimming (Sec. 3.5, Prop. 2)
-    int h_changed = 0;
-    int round = 0;
-    k_fill_inf<<<blocks_for(SN), 256, 0, st>>>(SN, fst);
-    k_fill_inf<<<blocks_for(SN), 256, 0, st>>>(SN, bst);
-    TRY(cudaGetLastError());
-    const int BATCH = 16;
-    for (;;) {
-        TRY(cudaMemsetAsync(flags, 0, sizeof(int), st));
-        for (int b = 0; b < BATCH; ++b, ++round) k_fwd_trim<<<blocks_for(SN), 256, 0, st>>>(g, SN, upmask, fst, round, flags);
-        TRY(cudaMemcpyAsync(&h_changed, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
-        TRY(cudaStreamSynchronize(st));
-        if (!h_changed) break;
-    }
-    for (round = 0;;) {
-        TRY(cudaMemsetAsync(flags, 0, sizeof(int), st));
-        for (int b = 0; b < BATCH; ++b, ++round) k_bwd_trim<<<blocks_for(SN), 256, 0, st>>>(g, SN, upmask, fst, bst, round, flags);
-        TRY(cudaMemcpyAsync(&h_changed, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
-        TRY(cudaStreamSynchronize(st));
-        if (!h_changed) break;
+    // ---- forward and backward trimming (Sec. 3.5, Prop. 2), frontier by frontier
+    TRY(sc.get(&act, SN));        // in-degree counters
+    TRY(sc.get(&list, SN));       // two frontier queues
+    TRY(sc.get(&color, SN));
+    {
+        const unsigned gs = (unsigned)std::max(1, t->num_sms * 8);
+        int *q[2] = {list, color};
+        int *nq = flags;          // flags[0], flags[1]: frontier sizes
+        auto rounds = [&](auto step) -> int {
+            for (int r = 0;; ++r) {
+                const int c = r & 1;
+                TRY(cudaMemsetAsync(nq + (c ^ 1), 0, sizeof(int), st));
+                step(q[c], nq + c, q[c ^ 1], nq + (c ^ 1), r);
+                if ((r & 31) == 31) {
+                    int h = 0;
+                    TRY(cudaMemcpyAsync(&h, nq + (c ^ 1), sizeof(int), cudaMemcpyDeviceToHost, st));
+                    TRY(cudaStreamSynchronize(st));
+                    if (h == 0) return EIK_OK;
+                }
+                if (r > (1 << 28)) { set_error("trimming did not terminate"); return fail(EIK_ERR_CYCLE); }
+            }
+        };
+        TRY(cudaMemsetAsync(flags, 0, 8 * sizeof(int), st));
+        k_trim_fwd_init<<<blocks_for(SN), 256, 0, st>>>(SN, upmask, act, fst, q[0], nq);
+        TRY(cudaGetLastError());
+        int rc = rounds([&](int *cur, int *ncur, int *next, int *nnext, int r) {
+            k_trim_fwd_step<<<gs, 256, 0, st>>>(g, upmask, act, fst, cur, ncur, next, nnext, r);
+        });
+        if (rc) return rc;
+        TRY(cudaGetLastError());
+        TRY(cudaMemsetAsync(flags, 0, 8 * sizeof(int), st));
+        k_trim_bwd_init<<<blocks_for(SN), 256, 0, st>>>(g, SN, upmask, fst, act, bst, q[0], nq);
+        TRY(cudaGetLastError());
+        rc = rounds([&](int *cur, int *ncur, int *next, int *nnext, int r) {
+            k_trim_bwd_step<<<gs, 256, 0, st>>>(g, upmask, fst, act, bst, cur, ncur, next, nnext, r);
+        });
+        if (rc) return rc;
+        TRY(cudaGetLastError());
     }
 
-    // ---- SCCs of the trimmed residual by colouring (Sec. 4.1)
-    TRY(sc.get(&act, SN));
-    TRY(sc.get(&color, SN));
-    TRY(sc.get(&inscc, SN));
-    TRY(sc.get(&list, SN));
-    TRY(cudaMemsetAsync(flags, 0, 8 * sizeof(int), st));
-    k_collect<<<blocks_for(SN), 256, 0, st>>>(SN, fst, bst, list, flags + 1, lab, act);
-    int nres = 0;
-    TRY(cudaMemcpyAsync(&nres, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-    TRY(cudaStreamSynchronize(st));
-    int outer = 0;
-    while (nres > 0) {
-        if (++outer > 1000000) { set_error("SCC colouring did not terminate"); return fail(EIK_ERR_CYCLE); }
-        k_color_init<<<blocks_for(nres), 256, 0, st>>>(list, nres, act, color, inscc);
-        for (;;) {
-            TRY(cudaMemsetAsync(flags, 0, sizeof(int), st));
-            for (int b = 0; b < 8; ++b) k_color_prop<<<blocks_for(nres), 256, 0, st>>>(g, list, nres, upmask, act, color, flags);
-            TRY(cudaMemcpyAsync(&h_changed, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
-            TRY(cudaStreamSynchronize(st));
-            if (!h_changed) break;
-        }
-        k_scc_roots<<<blocks_for(nres), 256, 0, st>>>(list, nres, act, color, inscc);
-        for (;;) {
-            TRY(cudaMemsetAsync(flags, 0, sizeof(int), st));
-            for (int b = 0; b < 8; ++b) k_scc_back<<<blocks_for(nres), 256, 0, st>>>(g, list, nres, upmask, act, color, inscc, flags);
-            TRY(cudaMemcpyAsync(&h_changed, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
-            TRY(cudaStreamSynchronize(st));
-            if (!h_changed) break;
-        }
-        TRY(cudaMemsetAsync(flags + 2, 0, sizeof(int), st));
-        k_scc_take<<<blocks_for(nres), 256, 0, st>>>(list, nres, act, color, inscc, lab, flags + 2);
-        int rem = 0;
-        TRY(cudaMemcpyAsync(&rem, flags + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+    // ---- SCCs of the residual (both closures) by Tarjan's algorithm (Sec. 4.1 [ref50]),
+    // one host thread per group of sources: the residual is a few percent of the vertices
+    {
+        unsigned char *rflag;
+        TRY(sc.get(&rflag, SN));
+        k_residual_flags<<<blocks_for(SN), 256, 0, st>>>(SN, fst, bst, rflag, lab);
+        TRY(cudaGetLastError());
+        size_t tb = 0;
+        thrust::counting_iterator<int> iota(0);
+        TRY(cub::DeviceSelect::Flagged(nullptr, tb, iota, rflag, list, flags + 2, (int)SN, st));
+        void *tmp;
+        TRY(sc.get((unsigned char **)&tmp, tb));
+        TRY(cub::DeviceSelect::Flagged(tmp, tb, iota, rflag, list, flags + 2, (int)SN, st));
+        int nres = 0;
+        TRY(cudaMemcpyAsync(&nres, flags + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
         TRY(cudaStreamSynchronize(st));
-        if (rem == 0) break;
+        if (nres > 0) {
+            unsigned char *dmask;
+            TRY(sc.get(&dmask, nres));
+            k_gather_masks<<<blocks_for(nres), 256, 0, st>>>(list, nres, upmask, dmask);
+            std::vector<int> hnodes(nres), hlab(nres);
+            std::vector<unsigned char> hmask(nres);
+            TRY(cudaMemcpyAsync(hnodes.data(), list, (size_t)nres * sizeof(int), cudaMemcpyDeviceToHost, st));
+            TRY(cudaMemcpyAsync(hmask.data(), dmask, (size_t)nres, cudaMemcpyDeviceToHost, st));
+            TRY(cudaStreamSynchronize(st));
+            // per source: its residual vertices are one contiguous range of the ascending list
+            std::vector<int> rs(S + 1);
+            for (int a = 0; a <= S; ++a)
+                rs[a] = (int)(std::lower_bound(hnodes.begin(), hnodes.end(), (long long)a * N < INF ? (int)(a * N) : INF) -
+                              hnodes.begin());
+            rs[S] = nres;
+            const int nth = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+            std::vector<std::thread> pool;
+            std::atomic<int> next{0};
+            for (int w = 0; w < nth; ++w)
+                pool.emplace_back([&]() {
+                    for (int a; (a = next.fetch_add(1)) < S;)
+                        if (rs[a + 1] > rs[a])
+                            tarjan_residual(g, hnodes.data() + rs[a], hmask.data() + rs[a], rs[a + 1] - rs[a],
+                                            hlab.data() + rs[a]);
+                });
+            for (auto &th : pool) th.join();
+            int *dlab;
+            TRY(sc.get(&dlab, nres));
+            TRY(cudaMemcpyAsync(dlab, hlab.data(), (size_t)nres * sizeof(int), cudaMemcpyHostToDevice, st));
+            k_scatter_labels<<<blocks_for(nres), 256, 0, st>>>(list, dlab, nres, lab);
+            TRY(cudaGetLastError());
+            TRY(cudaStreamSynchronize(st));   // the host vectors go out of scope
+        }
     }
     TRY(sc.get(&csize, SN));
     TRY(cudaMemsetAsync(csize, 0, SN * sizeof(int), st));
     k_comp_size<<<blocks_for(SN), 256, 0, st>>>(SN, lab, csize);
 
     // ---- canonical levels (longest path on the condensation)
+    const int BATCH = 16;
+    int round = 0;
     TRY(sc.get(&lvl, SN));
     TRY(sc.get(&asg, SN));
     TRY(sc.get(&cmax, SN));
