@@ -324,10 +324,9 @@ __global__ void k_comp_size(long long SN, const int *__restrict__ label, int *cs
 }
 
 // ---------------------------------------------------------------------------
-// Canonical levels (longest path in the condensation DAG), in rounds: a component is
-// assigned in round t once all of its external predecessor components were assigned
-// in earlier rounds; its level is 1 + the largest of theirs (0 without predecessor).
-// The per-component values live at the component's root vertex.
+// Canonical levels (longest path in the condensation DAG): a component's level is 1 +
+// the largest level among its external predecessor components (0 without one).  The
+// per-component values live at the component's root vertex.
 // ---------------------------------------------------------------------------
 __global__ void k_lvl_init(long long SN, const int *__restrict__ fst, const int *__restrict__ label, int *lvl, int *asg,
                            int *cmax, int *blk, int *list, int *count)
@@ -338,43 +337,10 @@ __global__ void k_lvl_init(long long SN, const int *__restrict__ fst, const int 
     // their Kahn round is their longest-path level
     if (fst[v] != INF) { lvl[v] = fst[v]; asg[v] = -1; }
     else {
-        if (label[v] == v) { asg[v] = INF; cmax[v] = -1; blk[v] = -1; }
+        if (label[v] == v) { asg[v] = INF; cmax[v] = -1; blk[v] = 0; }
         int k = atomicAdd(count, 1);
         list[k] = (int)v;
     }
-}
-
-__global__ void k_lvl_scan(GridDesc g, const int *list, int n, const unsigned char *__restrict__ upmask,
-                           const int *__restrict__ label, const int *lvl, const int *asg, int *cmax, int *blk, int t)
-{
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    int v = list[k];
-    int c = label[v];
-    if (asg[c] != INF) return;
-    int m = -1;
-    bool blocked = false;
-    for_preds(g, v, upmask[v], [&](long long u) {
-        int cu = label[u];
-        if (cu == c) return;
-        int au = asg[cu];
-        if (au >= t) blocked = true;       // unassigned, or assigned in this very round
-        else if (lvl[cu] > m) m = lvl[cu];
-    });
-    if (blocked) blk[c] = t;
-    if (m >= 0) atomicMax(&cmax[c], m);
-}
-
-__global__ void k_lvl_assign(const int *list, int n, const int *__restrict__ label, int *lvl, int *asg,
-                             const int *cmax, const int *blk, int t, int *assigned)
-{
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    int v = list[k];
-    if (label[v] != v || asg[v] != INF || blk[v] == t) return;
-    lvl[v] = cmax[v] + 1;
-    asg[v] = t;
-    atomicAdd(assigned, 1);
 }
 
 __global__ void k_node_level(long long SN, long long N, const int *__restrict__ label, const int *__restrict__ lvl,
@@ -623,6 +589,77 @@ __global__ void k_block_lu(const int4 *__restrict__ desc, const long long *__res
     }
 }
 
+// Longest-path levels of the components downstream of the cycles by component-level
+// Kahn with frontier queues: pend[c] counts the edges into component c from other
+// components of the level list, cmax[c] is the largest level among c's predecessors;
+// a component enters the frontier when its last such edge is resolved, takes level
+// cmax + 1, and resolves the edges leaving its members.  Values live at the root.
+__global__ void k_lvl_count(GridDesc g, const int *__restrict__ list, int n, const unsigned char *__restrict__ upmask,
+                            const int *__restrict__ fst, const int *__restrict__ label, int *pend, int *cmax)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const long long v = list[k];
+    const int c = label[v];
+    for_preds(g, v, upmask[v], [&](long long u) {
+        const int cu = label[u];
+        if (cu == c) return;
+        if (fst[u] != INF) atomicMax(&cmax[c], fst[u]);   // a trimmed singleton: its level is its Kahn round
+        else atomicAdd(&pend[c], 1);
+    });
+}
+
+__global__ void k_lvl_front0(const int *__restrict__ list, int n, const int *__restrict__ label,
+                             const int *__restrict__ pend, int *front, int *nfront)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int v = list[k];
+    if (label[v] == v && pend[v] == 0) front[atomicAdd(nfront, 1)] = v;
+}
+
+// list vertices that belong to a nontrivial component, and their roots
+__global__ void k_nontrivial_flags(const int *__restrict__ list, int n, const int *__restrict__ label,
+                                   const int *__restrict__ csize, unsigned char *flag, int *root)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int c = label[list[k]];
+    flag[k] = csize[c] > 1;
+    root[k] = c;
+}
+
+// members of the nontrivial components, grouped by root: moff[root] = first position
+__global__ void k_member_offsets(const int *__restrict__ roots, int n, int *moff)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && (i == 0 || roots[i] != roots[i - 1])) moff[roots[i]] = i;
+}
+
+__global__ void k_lvl_step(GridDesc g, const unsigned char *__restrict__ upmask, const int *__restrict__ label,
+                           const int *__restrict__ csize, const int *__restrict__ moff, const int *__restrict__ members,
+                           int *lvl, int *asg, int *cmax, int *pend, const int *__restrict__ cur, const int *ncur, int *next,
+                           int *nnext, int round)
+{
+    const int n = *ncur;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int c = cur[k];
+        const int L = cmax[c] + 1;
+        lvl[c] = L;
+        asg[c] = round;
+        const int sz = csize[c];
+        for (int m = 0; m < sz; ++m) {
+            const long long v = sz == 1 ? c : members[moff[c] + m];
+            for_succs(g, v, upmask, [&](long long u) {
+                const int cu = label[u];
+                if (cu == c) return;
+                atomicMax(&cmax[cu], L);
+                if (atomicSub(&pend[cu], 1) == 1) next[atomicAdd(nnext, 1)] = cu;
+            });
+        }
+    }
+}
+
 __global__ void k_check_assigned(long long SN, const int *label, const int *asg, int *bad)
 {
     long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -630,18 +667,32 @@ __global__ void k_check_assigned(long long SN, const int *label, const int *asg,
     if (label[v] == v && asg[v] == INF) atomicAdd(bad, 1);
 }
 
+// per-source sums of a per-vertex count: the lanes of a warp that belong to the same
+// source (almost always all of them) are summed first, one atomic per source and warp
+__device__ __forceinline__ void add_per_source(long long v, long long SN, long long N, unsigned long long x,
+                                               unsigned long long *sum)
+{
+    const long long a = v < SN ? v / N : -1;
+    const unsigned full = 0xffffffffu;
+    const long long a0 = __shfl_sync(full, a, 0);
+    if (__all_sync(full, a == a0)) {
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(full, x, o);
+        if ((threadIdx.x & 31) == 0 && a0 >= 0 && x) atomicAdd(&sum[a0], x);
+    } else if (a >= 0 && x) {
+        atomicAdd(&sum[a], x);
+    }
+}
+
 __global__ void k_count_roots(long long SN, long long N, const int *label, unsigned long long *nroots)
 {
-    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (v >= SN) return;
-    if (label[v] == v) atomicAdd(&nroots[v / N], 1ull);
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    add_per_source(v, SN, N, (v < SN && label[v] == v) ? 1ull : 0ull, nroots);
 }
 
 __global__ void k_count_edges(long long SN, long long N, const int *cnt, unsigned long long *ne)
 {
-    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (v >= SN) return;
-    atomicAdd(&ne[v / N], (unsigned long long)cnt[v]);
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    add_per_source(v, SN, N, v < SN ? (unsigned long long)cnt[v] : 0ull, ne);
 }
 
 __global__ void k_local_labels(long long SN, long long N, int *label)
@@ -793,17 +844,18 @@ inline unsigned blocks_for(long long n, int t = 256) { return (unsigned)((n + t 
 // source: `nodes` ascending (global indices), `masks` their upwind-face bits; the edges
 // are the upwind faces whose neighbour is also residual.  Writes for every vertex the
 // smallest global index of its strongly connected component (the canonical label).
-void tarjan_residual(const GridDesc &g, const int *nodes, const unsigned char *masks, int n, int *out)
+void tarjan_residual(const GridDesc &g, const int *nodes, const unsigned char *masks, int n, int *out,
+                     std::vector<int> &where)
 {
+    // where[local node] = position in `nodes` (a reusable [N] map, -1 outside the residual)
+    const long long base = (long long)nodes[0] / g.N * g.N;
+    for (int k = 0; k < n; ++k) where[nodes[k] - base] = k;
     std::vector<int> index(n, -1), low(n), stk;
     std::vector<char> on(n, 0);
     struct Frame { int v; int b; };
     std::vector<Frame> cs;
     int counter = 0;
-    auto find = [&](long long u) -> int {
-        const int *it = std::lower_bound(nodes, nodes + n, (int)u);
-        return (it != nodes + n && *it == u) ? (int)(it - nodes) : -1;
-    };
+    auto find = [&](long long u) -> int { return where[u - base]; };
     for (int r = 0; r < n; ++r) {
         if (index[r] >= 0) continue;
         index[r] = low[r] = counter++;
@@ -847,6 +899,7 @@ void tarjan_residual(const GridDesc &g, const int *nodes, const unsigned char *m
             if (!cs.empty()) { const int p = cs.back().v; low[p] = std::min(low[p], low[v]); }
         }
     }
+    for (int k = 0; k < n; ++k) where[nodes[k] - base] = -1;
 }
 
 }  // namespace
@@ -996,10 +1049,13 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
             std::atomic<int> next{0};
             for (int w = 0; w < nth; ++w)
                 pool.emplace_back([&]() {
+                    std::vector<int> where;
                     for (int a; (a = next.fetch_add(1)) < S;)
-                        if (rs[a + 1] > rs[a])
+                        if (rs[a + 1] > rs[a]) {
+                            if (where.empty()) where.assign((size_t)N, -1);
                             tarjan_residual(g, hnodes.data() + rs[a], hmask.data() + rs[a], rs[a + 1] - rs[a],
-                                            hlab.data() + rs[a]);
+                                            hlab.data() + rs[a], where);
+                        }
                 });
             for (auto &th : pool) th.join();
             int *dlab;
@@ -1015,8 +1071,6 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
     k_comp_size<<<blocks_for(SN), 256, 0, st>>>(SN, lab, csize);
 
     // ---- canonical levels (longest path on the condensation)
-    const int BATCH = 16;
-    int round = 0;
     TRY(sc.get(&lvl, SN));
     TRY(sc.get(&asg, SN));
     TRY(sc.get(&cmax, SN));
@@ -1027,17 +1081,64 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
     int nlst = 0;
     TRY(cudaMemcpyAsync(&nlst, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
-    for (round = 0; nlst > 0;) {
-        TRY(cudaMemsetAsync(flags + 3, 0, sizeof(int), st));
-        for (int b = 0; b < BATCH; ++b, ++round) {
-            k_lvl_scan<<<blocks_for(nlst), 256, 0, st>>>(g, list, nlst, upmask, lab, lvl, asg, cmax, blk, round);
-            k_lvl_assign<<<blocks_for(nlst), 256, 0, st>>>(list, nlst, lab, lvl, asg, cmax, blk, round, flags + 3);
-        }
-        int assigned = 0;
-        TRY(cudaMemcpyAsync(&assigned, flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (nlst > 0) {
+        // pend (in blk) and cmax of the components of the level list
+        k_lvl_count<<<blocks_for(nlst), 256, 0, st>>>(g, list, nlst, upmask, fst, lab, blk, cmax);
+        // members of the nontrivial components of the list, grouped by root
+        int *mroot, *members, *mroot_s, *members_s, *moff;
+        unsigned char *mflag;
+        TRY(sc.get(&mflag, nlst));
+        TRY(sc.get(&mroot, nlst));
+        k_nontrivial_flags<<<blocks_for(nlst), 256, 0, st>>>(list, nlst, lab, csize, mflag, mroot);
+        TRY(cudaGetLastError());
+        TRY(sc.get(&members, nlst));
+        TRY(sc.get(&members_s, nlst));
+        TRY(sc.get(&mroot_s, nlst));
+        size_t tb = 0;
+        TRY(cub::DeviceSelect::Flagged(nullptr, tb, list, mflag, members, flags + 5, nlst, st));
+        void *tmp;
+        TRY(sc.get((unsigned char **)&tmp, tb));
+        TRY(cub::DeviceSelect::Flagged(tmp, tb, list, mflag, members, flags + 5, nlst, st));
+        size_t tb2 = 0;
+        TRY(cub::DeviceSelect::Flagged(nullptr, tb2, mroot, mflag, mroot_s, flags + 6, nlst, st));
+        void *tmp2;
+        TRY(sc.get((unsigned char **)&tmp2, tb2));
+        TRY(cub::DeviceSelect::Flagged(tmp2, tb2, mroot, mflag, mroot_s, flags + 6, nlst, st));
+        int nmem = 0;
+        TRY(cudaMemcpyAsync(&nmem, flags + 5, sizeof(int), cudaMemcpyDeviceToHost, st));
         TRY(cudaStreamSynchronize(st));
-        if (assigned == 0) break;
-        if (round > 100000000) { set_error("level rounds did not terminate"); return fail(EIK_ERR_CYCLE); }
+        TRY(sc.get(&moff, SN));
+        if (nmem > 0) {
+            // group by root: stable sort of (root, node) pairs by root
+            size_t tb3 = 0;
+            TRY(cub::DeviceRadixSort::SortPairs(nullptr, tb3, mroot_s, mroot, members, members_s, nmem, 0, 32, st));
+            void *tmp3;
+            TRY(sc.get((unsigned char **)&tmp3, tb3));
+            TRY(cub::DeviceRadixSort::SortPairs(tmp3, tb3, mroot_s, mroot, members, members_s, nmem, 0, 32, st));
+            k_member_offsets<<<blocks_for(nmem), 256, 0, st>>>(mroot, nmem, moff);
+            TRY(cudaGetLastError());
+        }
+        // frontier rounds
+        const unsigned gs = (unsigned)std::max(1, t->num_sms * 8);
+        int *q[2] = {color, act};
+        int *nq = flags;
+        TRY(cudaMemsetAsync(flags, 0, 2 * sizeof(int), st));
+        k_lvl_front0<<<blocks_for(nlst), 256, 0, st>>>(list, nlst, lab, blk, q[0], nq);
+        TRY(cudaGetLastError());
+        for (int r = 0;; ++r) {
+            const int c = r & 1;
+            TRY(cudaMemsetAsync(nq + (c ^ 1), 0, sizeof(int), st));
+            k_lvl_step<<<gs, 256, 0, st>>>(g, upmask, lab, csize, moff, members_s, lvl, asg, cmax, blk, q[c], nq + c,
+                                           q[c ^ 1], nq + (c ^ 1), r);
+            if ((r & 31) == 31) {
+                int h = 0;
+                TRY(cudaMemcpyAsync(&h, nq + (c ^ 1), sizeof(int), cudaMemcpyDeviceToHost, st));
+                TRY(cudaStreamSynchronize(st));
+                if (h == 0) break;
+            }
+            if (r > (1 << 28)) { set_error("level rounds did not terminate"); return fail(EIK_ERR_CYCLE); }
+        }
+        TRY(cudaGetLastError());
     }
     // check every component assigned
     TRY(cudaMemsetAsync(flags + 4, 0, sizeof(int), st));
