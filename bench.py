@@ -345,8 +345,20 @@ def run_ours(args):
                   "largest_scc": max(x["largest"] for x in st), "edges_per_node": sum(x["edges"] for x in st) / (S * N)},
         "kernel_ms": {"fwd": round(mf, 4), "bwd": round(mb, 4)},
     }
-    print(json.dumps(out), flush=True)
     tan.free()
+    if not args.no_extras and world == 1:
+        # the other workloads of this path, recorded on the same line (setup times and the
+        # stress grids are not part of the headline value)
+        del p, y, d_rec, gvec, p_h, y_h, drec_h, g_h, p_d, y_d
+        torch.cuda.empty_cache()
+        for key, fn in (("gauss_newton_iteration_config4", gauss_newton_iteration_config4),
+                        ("stress_config5", lambda: stress_config5(check_oracle=not args.no_cpu))):
+            try:
+                out[key] = fn()
+            except Exception as e:   # an extra never takes the headline line down with it
+                out[key] = {"error": f"{type(e).__name__}: {e}"[:300]}
+            torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -481,72 +493,195 @@ def run_gn(args):
     tan.free()
 
 
-def run_stress(args):
+def stress_config5(steps: int = 3, check_oracle: bool = True, sweep: bool = True) -> dict:
     """Config 5, the uneven-batch stress case: three steep-hill grids (slopes up to about
-    55 deg), 101x101x51 (32 sources, R = 8), 161x121x61 (32, R = 32) and 201x201x101 (64,
-    R = 128; a [S][N][R] FP32 field is 134 GB there, so the right-hand sides go through the
-    traversal in chunks of 32).  Per grid: state (FP32 far field), build, then J p + J^T y
-    pairs timed with CUDA events.  value = all grids' node-updates / all grids' time."""
+    55 deg) -- 101x101x51 (32 sources, R = 8), 161x121x61 (32, R = 32), 201x201x101 (64,
+    R = 128) -- traversed together: J p of all three grids in ONE launch of the cluster
+    schedule and J^T y (summed over sources) in one more (tangent_apply_batch), with every
+    tangent's workspace holding all its right-hand sides.  Per grid: the error of J p and
+    J^T y against the FP64 oracle on a sampled source and four columns (the oracle builds
+    its tangent from the same state), and the node-updates/s of BTF against GPU
+    directional sweeping on a 4-source slice of the grid at R = min(R, 32)."""
     import torch
 
     from paper_2609_14982_b300 import eik
     from paper_2609_14982_b300 import workloads as W
-    torch.cuda.set_device(0)
-    grids, tot_upd, tot_ms = [], 0.0, 0.0
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    tans, ps, ys, info, wls, states = [], [], [], [], [], []
+    t0 = time.time()
     for w in range(3):
         wl = W.config5_grid(w)
         g = wl.grid
-        S, N, R = wl.S, g.N, wl.R
-        dg = eik.DeviceGrid(g)
-        s = torch.tensor(wl.s, device="cuda")
-        t0 = time.time()
+        dg = eik.DeviceGrid(g, device=dev)
+        s = torch.tensor(wl.s, device=dev)
+        ts = time.time()
         T, cyc = eik.eik_forward(dg, s, wl.src, opts=eik.default_opts(eik_fp32=1))
         torch.cuda.synchronize()
-        t_state = time.time() - t0
-        chunk = 32 if R > 32 else 0
-        t0 = time.time()
-        tan = eik.Tangent(dg, T, s, wl.src, rec=wl.rec, opts=eik.default_opts(rhs_chunk=chunk))
+        t_state = time.time() - ts
+        tb = time.time()
+        tan = eik.Tangent(dg, T, s, wl.src, rec=wl.rec)
         torch.cuda.synchronize()
-        t_build = time.time() - t0
+        t_build = time.time() - tb
+        st = [tan.stats(a) for a in range(wl.S)]
+        states.append((dg, s, T[:4].clone(), T[0].cpu().numpy()))
         del T
-        st = [tan.stats(a) for a in range(S)]
-        gen = torch.Generator("cuda").manual_seed(wl.seed)
-        p = torch.randn((N, R), device="cuda", generator=gen)
-        y = torch.randn((S, len(wl.rec), R), device="cuda", generator=gen)
-        for _ in range(max(args.warmup, 1)):
-            tan.apply(p, shared_model=True)
-            tan.apply_T(y, sum_sources=True)
-        steps = max(args.steps // 2, 3)
-        tf, tb = [], []
-        for _ in range(steps):
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            e[0].record()
-            tan.apply(p, shared_model=True)
-            e[1].record()
-            tan.apply_T(y, sum_sources=True)
-            e[2].record()
+        gen = torch.Generator(dev).manual_seed(wl.seed)
+        ps.append(torch.randn((g.N, wl.R), device=dev, generator=gen))
+        ys.append(torch.randn((wl.S, len(wl.rec), wl.R), device=dev, generator=gen))
+        tans.append(tan)
+        wls.append(wl)
+        info.append({"grid": list(g.n), "nodes": g.N, "sources": wl.S, "rhs": wl.R, "receivers": len(wl.rec),
+                     "max_slope_deg": round(wl.notes.get("max_slope_deg", 0.0), 1),
+                     "levels_max": max(x["levels"] for x in st), "nontrivial_scc": sum(x["nontrivial"] for x in st),
+                     "largest_scc": max(x["largest"] for x in st), "eik_forward_s": round(t_state, 2),
+                     "eik_cycles": cyc, "tangent_build_s": round(t_build, 2)})
+    # largest grid first: clusters take its (longest) sources first
+    order = [2, 1, 0]
+    bt = [tans[k] for k in order]
+    bp = [ps[k] for k in order]
+    by = [ys[k] for k in order]
+    eik.apply_batch(bt, bp)
+    eik.apply_T_batch(bt, by)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1, e2 in ev:
+        e0.record(stream)
+        eik.apply_batch(bt, bp)
+        e1.record(stream)
+        eik.apply_T_batch(bt, by)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    for t in tans:
+        t.status()
+    tf = statistics.median(a.elapsed_time(b) for a, b, _ in ev)
+    tbk = statistics.median(b.elapsed_time(c) for _, b, c in ev)
+    upd = sum(2.0 * t.N * t.S * wl.R for t, wl in zip(tans, wls))
+    out = {"workload": "3d-stress: 101x101x51 S32 R8 + 161x121x61 S32 R32 + 201x201x101 S64 R128",
+           "launch": "one cluster-schedule launch per direction for all three grids (tangent_apply_batch)",
+           "value": upd / ((tf + tbk) / 1e3), "unit": UNIT, "ms_fwd": round(tf, 3), "ms_bwd": round(tbk, 3),
+           "grids": info}
+    jp_all = eik.apply_batch(bt, bp)
+    torch.cuda.synchronize()
+    for k, w in enumerate(order):
+        tan, wl, (dg, s, T4, T0h) = tans[w], wls[w], states[w]
+        g = wl.grid
+        cols = [0, wl.R // 3, (2 * wl.R) // 3, wl.R - 1]
+        if check_oracle:
+            import oracle as O
+            _, G, _ = O.metric(g)
+            ot = O.build_tangent(g, G, T0h, wl.s, int(wl.src[0]))
+            pn = ps[w][:, cols].double().cpu().numpy()
+            ref = O.J([ot], wl.s, wl.rec, pn)[0]
+            got = jp_all[k][0][:, cols].double().cpu().numpy()
+            e_j = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+            # J^T of source 0 alone: data only on source 0, the source sum is then J_0^T y_0
+            y0 = torch.zeros((wl.S, len(wl.rec), 4), device=dev)
+            y0[0] = ys[w][0][:, cols]
+            g0, _ = tan.apply_T(y0.contiguous(), sum_sources=True)
+            refT = O.JT([ot], wl.s, wl.rec, y0[:1].double().cpu().numpy())
+            e_t = float(np.max(np.abs(g0.double().cpu().numpy() - refT)) / np.max(np.abs(refT)))
+            info[w]["err_vs_oracle"] = {"J": e_j, "JT": e_t, "source": 0, "columns": cols}
+        if sweep:
+            Rs = min(wl.R, 32)
+            small = eik.Tangent(dg, T4, s, wl.src[:4], rec=wl.rec)
+            q = torch.randn((4, g.N, Rs), device=dev, generator=torch.Generator(dev).manual_seed(wl.seed + 1))
+            xb = torch.empty_like(q)
+            so = eik.default_opts(sweep_tol=1e-6)
+            small.solve(q, out=xb); small.solve_T(q, out=xb)
+            small.sweep(q, transpose=False, opts=so, out=xb); small.sweep(q, transpose=True, opts=so, out=xb)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            e[0].record(stream)
+            small.solve(q, out=xb)
+            small.solve_T(q, out=xb)
+            e[1].record(stream)
+            _, c1 = small.sweep(q, transpose=False, opts=so, out=xb)
+            e[2].record(stream)
+            _, c2 = small.sweep(q, transpose=True, opts=so, out=xb)
+            e[3].record(stream)
             torch.cuda.synchronize()
-            tf.append(e[0].elapsed_time(e[1]))
-            tb.append(e[1].elapsed_time(e[2]))
-        tan.status()
-        ms = statistics.median(tf) + statistics.median(tb)
-        upd = 2.0 * N * S * R
-        tot_upd += upd * steps
-        tot_ms += sum(tf) + sum(tb)
-        grids.append({"grid": list(g.n), "nodes": N, "sources": S, "rhs": R, "receivers": len(wl.rec),
-                      "rhs_chunk": chunk, "max_slope_deg": round(wl.notes.get("max_slope_deg", 0.0), 1),
-                      "ms_fwd": round(statistics.median(tf), 3), "ms_bwd": round(statistics.median(tb), 3),
-                      "node_updates_per_s": upd / (ms / 1e3), "levels_max": max(x["levels"] for x in st),
-                      "nontrivial_scc": sum(x["nontrivial"] for x in st), "largest_scc": max(x["largest"] for x in st),
-                      "eik_forward_s": round(t_state, 2), "eik_cycles": cyc, "tangent_build_s": round(t_build, 2)})
-        del p, y
-        tan.free()
-        torch.cuda.empty_cache()
-    out = {"metric": METRIC, "value": tot_upd / (tot_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": steps,
-           "warmup": max(args.warmup, 1), "ms_per_step": tot_ms / steps, "higher_is_better": True,
+            small.status()
+            n_upd = 2.0 * 4 * g.N * Rs
+            t_btf, t_sw = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[3])
+            info[w]["sweep_vs_btf"] = {"sources": 4, "R": Rs, "tol": 1e-6, "cycles": [c1, c2],
+                                       "btf_node_updates_per_s": n_upd / (t_btf / 1e3),
+                                       "sweep_node_updates_per_s": n_upd / (t_sw / 1e3),
+                                       "btf_over_sweep": round(t_sw / t_btf, 1)}
+            small.free()
+            del q, xb
+    for t in tans:
+        t.free()
+    del tans, ps, ys, jp_all, states
+    torch.cuda.empty_cache()
+    out["total_s"] = round(time.time() - t0, 1)
+    return out
+
+
+def gauss_newton_iteration_config4(lsqr_iters: int = 20) -> dict:
+    """One outer Gauss-Newton iteration of Alg. 1 on the 201x201x101 grid (64 sources, 2500
+    receivers): Phase I (state solve with the FP32 far field, tangent_build) and the inner
+    solve of 20 LSQR iterations on J (FP64 vectors, every iteration replayed from a CUDA
+    graph).  Reports each part and the total."""
+    import torch
+
+    from paper_2609_14982_b300 import eik
+    from paper_2609_14982_b300 import workloads as W
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = W.config4()
+    g = wl.grid
+    dg = eik.DeviceGrid(g, device=dev)
+    s = torch.tensor(wl.s, device=dev)
+    b = torch.randn((wl.S, len(wl.rec)), device=dev, dtype=torch.float64,
+                    generator=torch.Generator(dev).manual_seed(20264))
+    # module load and first allocations outside the timed iteration
+    eik.eik_forward(dg, s, wl.src[:1], opts=eik.default_opts(eik_fp32=1, eik_max_cycles=4000))
+    torch.cuda.synchronize()
+    t0 = time.time()
+    T, cyc = eik.eik_forward(dg, s, wl.src, opts=eik.default_opts(eik_fp32=1))
+    torch.cuda.synchronize()
+    t1 = time.time()
+    tan = eik.Tangent(dg, T, s, wl.src, rec=wl.rec)
+    torch.cuda.synchronize()
+    t2 = time.time()
+    del T
+    side = torch.cuda.Stream(dev)
+    with torch.cuda.stream(side):
+        L = eik.LSQR(tan, dtype=torch.float64)
+        L.start(b)
+        L.iterate(lsqr_iters, use_graph=True)
+        _, sc = L.solution()
+    side.synchronize()
+    t3 = time.time()
+    # the same iterations once more, graph already captured: the steady-state cost
+    with torch.cuda.stream(side):
+        L.start(b)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        L.iterate(lsqr_iters, use_graph=True)
+        e1.record(side)
+    side.synchronize()
+    tan.status()
+    ms_iter = e0.elapsed_time(e1) / lsqr_iters
+    L.free()
+    tan.free()
+    torch.cuda.empty_cache()
+    return {"workload": "3d-201x201x101-S64, 2500 receivers: state + tangent_build + 20 LSQR iterations",
+            "eik_forward_s": round(t1 - t0, 3), "eik_cycles": cyc, "tangent_build_s": round(t2 - t1, 3),
+            "lsqr_first_20_s": round(t3 - t2, 3), "lsqr_ms_per_iteration": round(ms_iter, 3),
+            "iteration_total_s": round(t3 - t0, 3), "lsqr_phibar": sc["phibar"],
+            "source_nodes_per_s_build": wl.S * g.N / (t2 - t1)}
+
+
+def run_stress(args):
+    """Config 5 alone as one JSON line (see stress_config5)."""
+    import torch
+    torch.cuda.set_device(0)
+    r = stress_config5(steps=max(args.steps // 2, 3), check_oracle=not args.no_cpu, sweep=not args.no_sweep)
+    out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": max(args.steps // 2, 3),
+           "warmup": 1, "ms_per_step": r["ms_fwd"] + r["ms_bwd"], "higher_is_better": True,
            "dtype": "f32+f64blocks", "data": "synthetic (seeded steep-hill recipe; no public dataset)",
-           "config": {"workload": "3d-stress: 101x101x51 S32 R8 + 161x121x61 S32 R32 + 201x201x101 S64 R128",
-                      "grids": grids}}
+           "config": {"workload": r["workload"], "launch": r["launch"], "grids": r["grids"]}}
     print(json.dumps(out), flush=True)
 
 
@@ -731,6 +866,8 @@ def main():
     ap.add_argument("--level-waits", action="store_true",
                     help="persistent items wait for their whole previous level, not only their upstream items")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the Gauss-Newton iteration and the three-grid stress batch on the headline line")
     ap.add_argument("--sweep-tol", type=float, default=1e-6,
                     help="sweeping baseline: stop at max |dx| <= tol max |x| over a cycle (FP32 path)")
     ap.add_argument("--no-cpu", action="store_true")
