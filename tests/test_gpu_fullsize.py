@@ -1,11 +1,12 @@
 """GPU parity at the benchmark's full size (101 x 101 x 51, 25 sources, R = 64, persistent
 schedule, FP32 substitution with FP64 blocks), in the launch configuration bench.py times.
 
-Two sources are compared output by output with the oracle: the oracle solves their
-states itself (CPU sweeping), the device builds its tangent from those oracle states,
-and structure (bit for bit), J p at the receivers and J^T y are compared over all
-nodes.  All 25 sources are checked by properties that hold at any size: the scaling
-identity dT = -T for dv = v (Sec. 3.2) and the adjoint pairing (Sec. 4.4)."""
+Every one of the 25 sources is compared output by output with the oracle: the oracle
+solves each state itself (CPU sweeping, in a spawn-context process pool), the device
+builds one tangent from those 25 oracle states, and structure (bit for bit), J p at the
+receivers and each source's J_a^T y_a over all nodes are compared.  All sources are
+also checked by properties that hold at any size: the scaling identity dT = -T for
+dv = v (Sec. 3.2) and the adjoint pairing (Sec. 4.4)."""
 import numpy as np
 import pytest
 import torch
@@ -73,6 +74,54 @@ def test_fullsize_sampled_sources_match_oracle(oracle_mod, sampled, dtype):
     assert np.max(np.abs(drec.double().cpu().numpy() - ref)) <= tol * np.max(np.abs(ref))
     refT = oracle_mod.JT(otans, wl.s, wl.rec, y.double().cpu().numpy())
     assert np.max(np.abs(gsum.double().cpu().numpy() - refT)) <= tol * np.max(np.abs(refT))
+
+
+@pytest.fixture(scope="module")
+def every_source():
+    """Oracle states, structure and J / J^T columns of all 25 sources (process pool)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    wl = W.config3()
+    R = 64
+    rng = np.random.default_rng(25)
+    p = rng.standard_normal((wl.grid.N, R)).astype(np.float32)
+    y = rng.standard_normal((len(wl.src), len(wl.rec), R)).astype(np.float32)
+    cols = [0, 17, 40, 63]
+    from tests._oracle_pool import source_reference
+    pc = p[:, cols].astype(np.float64)
+    jobs = [(a, pc, y[a][:, cols].astype(np.float64)) for a in range(len(wl.src))]
+    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
+        res = sorted(ex.map(source_reference, jobs), key=lambda r: r[0])
+    return wl, p, y, cols, res
+
+
+def test_fullsize_every_source_matches_oracle(every_source):
+    """All 25 sources, FP32 with FP64 blocks (the benchmark path): structure bit for bit,
+    J p at the receivers and J_a^T y_a over all nodes within 1e-5 of the oracle."""
+    wl, p, y, cols, res = every_source
+    g = wl.grid
+    dg = eik.DeviceGrid(g)
+    Ts = np.stack([r[1] for r in res])
+    tan = eik.Tangent(dg, torch.tensor(Ts, device=DEV), torch.tensor(wl.s, device=DEV), wl.src, rec=wl.rec)
+    for a, r in enumerate(res):
+        ex = tan.export(a)
+        assert np.array_equal(ex["label"], r[2]) and np.array_equal(ex["perm"], r[3]), a
+        assert np.array_equal(ex["level_ptr"], r[4]), a
+    pd = torch.tensor(p, device=DEV)
+    yd = torch.tensor(y, device=DEV)
+    _, drec = tan.apply(pd, shared_model=True)
+    ga, _ = tan.apply_T(yd, sum_sources=False)
+    tan.status()
+    drec = drec[:, :, cols].double().cpu().numpy()
+    ga = ga[:, :, cols].double().cpu().numpy()
+    worst_j = worst_t = 0.0
+    for a, r in enumerate(res):
+        ej = np.max(np.abs(drec[a] - r[5])) / np.max(np.abs(r[5]))
+        et = np.max(np.abs(ga[a] - r[6])) / np.max(np.abs(r[6]))
+        worst_j, worst_t = max(worst_j, ej), max(worst_t, et)
+        assert ej <= 1e-5 and et <= 1e-5, (a, ej, et)
+    print(f"25 sources: worst J rel err {worst_j:.2e}, worst J^T rel err {worst_t:.2e}")
 
 
 def test_fullsize_scaling_identity_all_sources(full):
