@@ -19,18 +19,20 @@ def bench():
 
 
 def test_algorithmic_bytes_closed_form(bench):
-    """At R = 64 FP32 with ~2.96 edges per node the forward call moves 8 + 36/R bytes per
-    node-update (p read, dT written, structure shared by the R columns), the reverse call
-    4 + 36/R plus the receiver data and g."""
+    """At R = 64 FP32 with ~2.96 edges per node: the forward call reads the shared model p
+    once (4 / S bytes per node-update), writes dT (4) and reads the structure once, shared
+    by the R columns; the reverse call writes lam (4) and g once (4 / S), reads the
+    receiver data and the structure.  The per-source-input figure 8 + 36/R is kept beside."""
     S, N, R, n_rec = 25, 1000, 64, 10
     st = [{"edges": 2960} for _ in range(S)]
     ab = bench.algorithmic_bytes(st, R, 4, S, N, n_rec)
     struct = 16 + 2.96 * 8
     assert ab["updates"] == S * N * R
-    assert ab["fwd_per_update"] == pytest.approx(8 + struct / R + n_rec * 4 / N, rel=1e-12)
+    assert ab["fwd_per_update"] == pytest.approx(4 + 4 / S + struct / R + n_rec * 4 / N, rel=1e-12)
     assert ab["bwd_per_update"] == pytest.approx(4 + struct / R + n_rec * 4 / N + 4 / S, rel=1e-12)
-    # the published per-update figure of the 3-D workload
-    assert 8.5 < 8 + struct / R < 8.7
+    assert ab["fwd_per_update_input_per_source"] == pytest.approx(8 + struct / R + n_rec * 4 / N, rel=1e-12)
+    # the method's per-update bytes of the 3-D workload (R = 64, S = 25): about 4.78
+    assert 4.7 < 4 + 4 / S + struct / R < 4.85
 
 
 def test_traffic_record_requires_matching_source_hash(bench, tmp_path, monkeypatch):
