@@ -310,11 +310,15 @@ def config2() -> Workload:
                     {"max_slope_deg": float(slope)})
 
 
-def _config3d(name, n, Lxy, H, period, seed, hill_h=1.2, hill_sigma=3.0, rms=0.2) -> Grid:
+def _config3d(name, n, Lxy, H, period, seed, hill_h=1.2, hill_sigma=3.0, rms=0.2, stride=1) -> Grid:
+    """The 3-D recipe on an n grid; with stride > 1 the random surface is drawn on the grid
+    refined stride times and sampled at every stride-th node, so the coarse grid's nodes
+    lie on the fine grid's surface (a refinement pair of one model)."""
     rng = np.random.default_rng(seed)
     nx, ny = n[0], n[1]
+    fx, fy = stride * (nx - 1) + 1, stride * (ny - 1) + 1
+    field2 = gaussian_field_2d(fx, fy, Lxy / (fx - 1), Lxy / (fy - 1), 3.0, rms, rng)[::stride, ::stride]
     dx, dy = Lxy / (nx - 1), Lxy / (ny - 1)
-    field2 = gaussian_field_2d(nx, ny, dx, dy, 3.0, rms, rng)
     xc = yc = Lxy / 2
 
     def elev_grid():
@@ -371,6 +375,23 @@ def config4() -> Workload:
                    dtype=np.int32)
     return Workload("3d-201x201x101-S64-lsqr", g, 1.0 / v, src, rec, 1, seed,
                     {"max_slope_deg": slope})
+
+
+def config4_refinement(level: int, nsrc: int = 4) -> Workload:
+    """The config-4 model (201x201x101 over 40x40x15 km, 3 km checkerboard) at full size
+    (level 1) or on the 101x101x51 grid whose nodes are every second node of it (level 0),
+    with 4 sources and the 2500 receivers on nodes both grids share (the finite-difference
+    check of the slowness -> traveltime function at two resolutions)."""
+    seed = 20264
+    stride = 1 if level == 1 else 2
+    n = (201, 201, 101) if level == 1 else (101, 101, 51)
+    g, slope = _config3d("3d", n, 40.0, 15.0, 3.0, seed, stride=stride)
+    v = _velocity3d(g, 3.0)
+    fine = [(12, 12), (62, 112), (112, 62), (162, 162)][:nsrc]
+    src = np.array([_surface_index(g, a // stride, b // stride) for a, b in fine], dtype=np.int32)
+    rec = np.array([_surface_index(g, (4 * a + 2) // stride, (4 * b + 2) // stride) for a in range(50) for b in range(50)],
+                   dtype=np.int32)
+    return Workload(f"3d-config4-model-{n[0]}x{n[1]}x{n[2]}", g, 1.0 / v, src, rec, 1, seed, {"max_slope_deg": slope})
 
 
 def config5_grid(which: int) -> Workload:
