@@ -186,6 +186,21 @@ def run_ours(args):
     st = [tan.stats(a) for a in range(S)]
 
     dtype = torch.float32
+    schedule, pass_units, tuned = args.schedule, args.pass_units, None
+    if args.autotune:
+        # time each schedule's default and a few variants on this tangent (one J p + J^T y
+        # pair each, CUDA events) and keep the fastest for the timed region
+        from paper_2609_14982_b300.autotune import autotune, quick_candidates
+        rec = autotune(tan, R, dtype, reps=3, cache_path=None, cands=quick_candidates(R, dtype), seed=rank)
+        tuned = {"setting": rec["setting"], "ms": round(rec["ms"], 3), "tune_s": round(rec["tune_s"], 2),
+                 "tried": [{k: v for k, v in c.items() if k in ("ms", "schedule", "pass_units", "block_lu_min",
+                                                                 "cluster_size")} for c in rec["tried"]]}
+        for c in tuned["tried"]:
+            c["ms"] = round(c["ms"], 3)
+        names = {eik.SCHED_PERSISTENT: "persistent", eik.SCHED_LEVELS: "levels", eik.SCHED_STAGED: "staged",
+                 eik.SCHED_CLUSTER: "cluster"}
+        schedule = names[rec["setting"]["schedule"]]
+        pass_units = rec["setting"].get("pass_units", 0)
     gen = torch.Generator(dev).manual_seed(20263 + rank)
     p = torch.randn((N, R), device=dev, dtype=dtype, generator=gen)
     y = torch.randn((S, n_rec, R), device=dev, dtype=dtype, generator=gen)
@@ -292,9 +307,10 @@ def run_ours(args):
     dom, other = "fwd", "bwd"
     dom_ms = mf
     achieved = ab[dom] / (dom_ms / 1e3) / 1e9
-    kname = {"persistent": "k_traverse_persistent<float,4,%s>", "levels": "k_traverse_level<float,4,%s,1>",
-             "staged": "k_traverse_staged<float,4,%s>",
-             "cluster": "k_traverse_cluster<float,4,%s," + str(args.pass_units or 4) + ">"}[args.schedule]
+    kname = {"persistent": "k_traverse_persistent<float,4,%s>" if pass_units <= 1 else
+                           "k_traverse_persistent<float,4,%s," + str(min(pass_units, 4)) + ",1>",
+             "levels": "k_traverse_level<float,4,%s,1>", "staged": "k_traverse_staged<float,4,%s>",
+             "cluster": "k_traverse_cluster<float,4,%s," + str(pass_units or 4) + ">"}[schedule]
     kname = kname % ("false" if dom == "fwd" else "true")
     tpu = measured_traffic(dom, kname)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -340,12 +356,13 @@ def run_ours(args):
         "data": "synthetic (seeded recipe of the 3-D tomography-scale config; no public dataset)",
         "config": {"workload": workload, "grid": list(g.n), "nodes": N, "sources_per_gpu": S, "rhs": R,
                    "receivers": n_rec, "precision": "FP32 substitution, FP64 SCC blocks",
-                   "schedule": args.schedule, "waits": "levels" if args.level_waits else "items", "l2": "inputs larger than L2 (dT/lam 3.3 GB per direction)",
+                   "schedule": schedule, "autotuned": tuned,
+                   "waits": "levels" if args.level_waits else "items", "l2": "inputs larger than L2 (dT/lam 3.3 GB per direction)",
                    "parallelism": f"source-sharded x{world}" if world > 1 else "single GPU"},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": upd_step / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * (3 if args.schedule in ("persistent", "cluster") else (2 * max(x["levels"] for x in st) + 3)),
+        "gpu_launches": args.steps * (3 if schedule in ("persistent", "cluster") else (2 * max(x["levels"] for x in st) + 3)),
         "clocks": clocks,
         "sweep_baseline": sweep,
         "setup": {"eik_forward_s": round(t_state, 3), "eik_cycles": cyc, "tangent_build_s": round(t_setup, 3),
@@ -866,6 +883,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--schedule", choices=["persistent", "levels", "staged", "cluster"], default="persistent")
+    ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
+                    help="pick the traversal setting by timing a short candidate list before the timed region")
     ap.add_argument("--cluster-size", type=int, default=0, help="cluster schedule: CTAs per cluster (0 = auto)")
     ap.add_argument("--cluster-threads", type=int, default=0, help="cluster schedule: threads per CTA (0 = 256)")
     ap.add_argument("--pass-units", type=int, default=0, help="cluster schedule: units per thread per round (2 or 4)")

@@ -108,6 +108,12 @@ typedef struct {
     int pass_units;            /* most right-hand-side vectors a thread of the cluster schedule
                                   carries for one position: 1, 2 or 4 (default 0 = 4); a thread
                                   carries 4 / that many positions per round */
+    /* SCC block solves */
+    int block_lu_min;          /* blocks of at least this many nodes are solved by FP64 forward and
+                                  back substitution with their partial-pivot LU factors (one warp
+                                  per right-hand side); smaller blocks multiply by the explicit
+                                  inverse formed from the same factors (default 64; 0: always the
+                                  inverse) */
 } eik_opts;
 
 typedef struct {

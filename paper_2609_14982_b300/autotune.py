@@ -2,11 +2,18 @@
 
 The structure of a tangent is fixed at build time; how it is traversed is not.  This
 module times one J p and one J^T y (CUDA events on the current stream) for each
-candidate run-time setting -- schedule (persistent item queue or graph-replayed
-per-level launches), right-hand-side chunk, persistent CTAs per SM, per-item or
-per-level waits -- applies the
-fastest with tangent_tune and caches the choice per (grid size, sources, levels, R,
-dtype) in a JSON file.
+candidate run-time setting and applies the fastest with tangent_tune, caching the choice
+per (grid size, sources, levels, R, dtype) in a JSON file.  The knobs:
+  schedule           persistent item queue, cluster (one cluster per source, a hardware
+                     barrier per level) or graph-replayed per-level launches;
+  rhs_chunk          right-hand-side columns per traversal pass;
+  threads per level  cluster schedule: cluster_size CTAs x cluster_threads threads work on
+                     one source's level; persistent schedule: CTAs per SM (ctas_per_sm);
+  lane groups        pass_units: right-hand-side vectors a thread carries per position;
+  block tiling       block_lu_min: SCC blocks of at least this size are solved by
+                     column-parallel substitution with the LU factors instead of the
+                     explicit inverse;
+  waits              per-item dependencies or whole previous level (persistent).
 """
 from __future__ import annotations
 
@@ -28,6 +35,7 @@ def _key(tan, R: int, dtype) -> str:
 
 
 def candidates(R: int, dtype) -> list:
+    """The full search space (used by autotune when no candidates are given)."""
     unit = 4 if dtype == torch.float32 else 2
     chunks = [0] + [c for c in (R // 2, R // 4) if c >= unit and c % unit == 0 and c < R]
     out = []
@@ -36,8 +44,31 @@ def candidates(R: int, dtype) -> list:
         out.append({"schedule": eik.SCHED_STAGED, "ctas_per_sm": 0, "rhs_chunk": ch})
         for per_sm in (0, 1, 2):
             for deps in (1, 0):
-                out.append({"schedule": eik.SCHED_PERSISTENT, "ctas_per_sm": per_sm, "rhs_chunk": ch,
-                            "item_deps": deps})
+                for pu in (1, 2):
+                    out.append({"schedule": eik.SCHED_PERSISTENT, "ctas_per_sm": per_sm, "rhs_chunk": ch,
+                                "item_deps": deps, "pass_units": pu})
+        for cs in (0, 4, 8, 16):
+            for ct in (128, 256):
+                for pu in (2, 4):
+                    out.append({"schedule": eik.SCHED_CLUSTER, "rhs_chunk": ch, "cluster_size": cs,
+                                "cluster_threads": ct, "pass_units": pu})
+        for blk in (0, 64):
+            out.append({"schedule": eik.SCHED_PERSISTENT, "rhs_chunk": ch, "block_lu_min": blk})
+    return out
+
+
+def quick_candidates(R: int, dtype) -> list:
+    """A short list for callers that tune on every run (the benchmark): the defaults of
+    each schedule, the cluster schedule at two sizes, and the lane-group and
+    block-tiling variants of the persistent schedule."""
+    base = {"rhs_chunk": 0, "ctas_per_sm": 0, "item_deps": 1, "pass_units": 0, "cluster_size": 0,
+            "cluster_threads": 0, "block_lu_min": 0}
+    out = [dict(base, schedule=eik.SCHED_PERSISTENT),
+           dict(base, schedule=eik.SCHED_PERSISTENT, pass_units=2),
+           dict(base, schedule=eik.SCHED_PERSISTENT, block_lu_min=64),
+           dict(base, schedule=eik.SCHED_CLUSTER),
+           dict(base, schedule=eik.SCHED_CLUSTER, cluster_size=8, pass_units=2),
+           dict(base, schedule=eik.SCHED_LEVELS)]
     return out
 
 

@@ -41,6 +41,7 @@ void eik_opts_default(eik_opts *o)
     o->eik_fp32 = 0;
     o->eik_fp64_radius = 8.0;
     o->item_deps = 1;
+    o->block_lu_min = 64;
 }
 
 const char *eik_last_error(void) { return eik::last_error(); }
@@ -261,7 +262,7 @@ int tangent_tune(eik_tangent *tt, const eik_opts *o)
 {
     if (!tt || !o) { eik::set_error("bad tangent_tune arguments"); return EIK_ERR_INVALID; }
     if (o->schedule < EIK_SCHED_PERSISTENT || o->schedule > EIK_SCHED_CLUSTER) { eik::set_error("bad schedule"); return EIK_ERR_INVALID; }
-    if (o->rhs_chunk < 0 || o->ctas_per_sm < 0 || !(o->wait_timeout_s > 0)) { eik::set_error("bad tuning values"); return EIK_ERR_INVALID; }
+    if (o->rhs_chunk < 0 || o->ctas_per_sm < 0 || !(o->wait_timeout_s > 0) || o->block_lu_min < 0) { eik::set_error("bad tuning values"); return EIK_ERR_INVALID; }
     Tangent *t = tt->impl;
     t->opts.schedule = o->schedule;
     t->opts.ctas_per_sm = o->ctas_per_sm;
@@ -271,6 +272,7 @@ int tangent_tune(eik_tangent *tt, const eik_opts *o)
     t->opts.cluster_size = o->cluster_size;
     t->opts.cluster_threads = o->cluster_threads;
     t->opts.pass_units = o->pass_units;
+    t->opts.block_lu_min = o->block_lu_min;
     return EIK_OK;
 }
 

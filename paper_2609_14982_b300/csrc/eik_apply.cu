@@ -79,6 +79,9 @@ struct TravParams {
     const int4 *blk_desc;
     const long long *blk_off;
     const double *binv;    // block inverses
+    const double *lu;      // block LU factors (P A_C = L U, rows swapped in place) and pivots
+    const int *piv;
+    int blk_lu_min;        // blocks of at least this size use the LU substitution (0: never)
     double *ws;
     unsigned long long timeout_ns;
     // cluster schedule: [S][maxL+1] first position / first block of each level, [S] level
@@ -236,6 +239,69 @@ __device__ __forceinline__ void run_singletons(const TravParams &P, const Stage<
 // independent dot product instead of a k-step triangular sweep.
 struct CtaSync { __device__ void operator()() const { __syncthreads(); } };
 
+// FP64 substitution with a block's partial-pivot factors P A_C = L U (large blocks), one
+// warp per right-hand-side column, the dot products split over the lanes:
+//   A_C x = b:    apply the row swaps to b, L y = P b (unit lower), U x = y;
+//   A_C^T x = b:  U^T z = b, L^T w = z, then undo the row swaps (x = P^T w).
+// W holds b on entry and x on exit, [k][R] row-major.
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ void block_lu_solve(const double *__restrict__ LU, const int *__restrict__ piv, int k, double *W, int R,
+                               bool tr, int tid, int nthr)
+{
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+    for (int r = warp; r < R; r += nwarp) {
+        double *x = W + r;
+        if (!tr) {
+            if (lane == 0)
+                for (int m = 0; m < k; ++m) {
+                    const int q = piv[m];
+                    if (q != m) { const double t = x[(long long)m * R]; x[(long long)m * R] = x[(long long)q * R]; x[(long long)q * R] = t; }
+                }
+            __syncwarp();
+            for (int m = 1; m < k; ++m) {
+                double acc = 0.0;
+                for (int j = lane; j < m; j += 32) acc += LU[(long long)m * k + j] * x[(long long)j * R];
+                acc = warp_sum_d(acc);
+                if (lane == 0) x[(long long)m * R] -= acc;
+                __syncwarp();
+            }
+            for (int m = k - 1; m >= 0; --m) {
+                double acc = 0.0;
+                for (int j = m + 1 + lane; j < k; j += 32) acc += LU[(long long)m * k + j] * x[(long long)j * R];
+                acc = warp_sum_d(acc);
+                if (lane == 0) x[(long long)m * R] = (x[(long long)m * R] - acc) / LU[(long long)m * k + m];
+                __syncwarp();
+            }
+        } else {
+            for (int m = 0; m < k; ++m) {
+                double acc = 0.0;
+                for (int j = lane; j < m; j += 32) acc += LU[(long long)j * k + m] * x[(long long)j * R];
+                acc = warp_sum_d(acc);
+                if (lane == 0) x[(long long)m * R] = (x[(long long)m * R] - acc) / LU[(long long)m * k + m];
+                __syncwarp();
+            }
+            for (int m = k - 2; m >= 0; --m) {
+                double acc = 0.0;
+                for (int j = m + 1 + lane; j < k; j += 32) acc += LU[(long long)j * k + m] * x[(long long)j * R];
+                acc = warp_sum_d(acc);
+                if (lane == 0) x[(long long)m * R] -= acc;
+                __syncwarp();
+            }
+            if (lane == 0)
+                for (int m = k - 1; m >= 0; --m) {
+                    const int q = piv[m];
+                    if (q != m) { const double t = x[(long long)m * R]; x[(long long)m * R] = x[(long long)q * R]; x[(long long)q * R] = t; }
+                }
+            __syncwarp();
+        }
+    }
+}
+
 // the solve runs on threads tid = 0 .. nthr-1 of the CTA, which sync() synchronises
 template <typename T, bool TR, typename Sync = CtaSync>
 __device__ void run_block(const TravParams &P, int a, int b, int tid = threadIdx.x, int nthr = blockDim.x,
@@ -275,10 +341,17 @@ __device__ void run_block(const TravParams &P, int a, int b, int tid = threadIdx
         W[(long long)m * R + r] = acc;
     }
     sync();
+    const bool by_lu = P.blk_lu_min > 0 && k >= P.blk_lu_min;
+    if (by_lu) {
+        block_lu_solve(P.lu + luo, P.piv + P.blk_off[3 * b + 1], k, W, R, TR, tid, nthr);
+        sync();
+    }
     for (long long idx = tid; idx < (long long)k * R; idx += nthr) {
         const int m = (int)(idx / R), r = (int)(idx % R);
         double val = 0.0;
-        if (!TR) {
+        if (by_lu) {
+            val = W[(long long)m * R + r];
+        } else if (!TR) {
             const double *row = Ainv + (long long)m * k;
             for (int c = 0; c < k; ++c) val += row[c] * W[(long long)c * R + r];
         } else {
@@ -1819,6 +1892,7 @@ static TravParams make_params(Tangent *t, bool TR, int mode, const void *inp, in
     P.ndeps = t->opts.item_deps && t->holds.empty() ? (TR ? t->ndeps_bwd : t->ndeps_fwd) : nullptr;
     P.item_done = t->item_done;
     P.blk_desc = t->blk_desc; P.blk_off = t->blk_off; P.binv = t->binv; P.ws = t->ws_blk;
+    P.lu = t->lu; P.piv = t->piv; P.blk_lu_min = t->opts.block_lu_min;
     P.timeout_ns = (unsigned long long)(t->opts.wait_timeout_s * 1e9);
     P.lvl = t->lvl_d; P.blk_lvl = t->blk_lvl_d; P.nlev = t->nlev_d; P.order = t->order_d;
     return P;

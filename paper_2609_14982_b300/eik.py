@@ -48,7 +48,8 @@ class Opts(C.Structure):
                 ("eik_tol", C.c_double), ("eik_max_cycles", C.c_int), ("eik_src_radius", C.c_double),
                 ("sweep_tol", C.c_double), ("sweep_max_cycles", C.c_int), ("rhs_chunk", C.c_int),
                 ("eik_fp32", C.c_int), ("eik_fp64_radius", C.c_double), ("item_deps", C.c_int),
-                ("cluster_size", C.c_int), ("cluster_threads", C.c_int), ("pass_units", C.c_int)]
+                ("cluster_size", C.c_int), ("cluster_threads", C.c_int), ("pass_units", C.c_int),
+                ("block_lu_min", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -349,10 +350,10 @@ class Tangent:
 
     def tune(self, **kw):
         """Change run-time options (schedule, ctas_per_sm, rhs_chunk, wait_timeout_s, item_deps,
-        cluster_size, cluster_threads, pass_units)."""
+        cluster_size, cluster_threads, pass_units, block_lu_min)."""
         for k, v in kw.items():
             if k not in ("schedule", "ctas_per_sm", "rhs_chunk", "wait_timeout_s", "item_deps", "cluster_size",
-                         "cluster_threads", "pass_units"):
+                         "cluster_threads", "pass_units", "block_lu_min"):
                 raise KeyError(k)
             setattr(self.opts, k, v)
         _check(lib().tangent_tune(self.h, C.byref(self.opts)))
