@@ -19,6 +19,9 @@ What it computes (paper sections in brackets):
     relative damping S_k) and LSMR on it                               [Sec. 4.5]
   * the node <- cell averaging map of a cell-based velocity model      [Sec. 5.3]
   * multilinear sampling of off-grid receivers (P, P^T) in J, J^T      [Sec. 4.4]
+  * off-grid point sources: the state from the interpolated source
+    slowness, differentiated seed rows, and the direct term D_a for
+    receivers inside the source cell                                  [Sec. 3.1, 3.2, 4.4]
 
 Where the paper leaves a detail open the oracle takes one stated reading (face
 averages, boundary stencils, canonical order); those readings are pinned by the
@@ -79,6 +82,10 @@ def lib():
         L.or_kahn_residual.restype = Lg
         L.or_eik_lf.argtypes = [I, _pi, _pd, _pd, _pd, Lg, D, D, Lg, _pd]
         L.or_eik_lf.restype = Lg
+        L.or_eik_lf_point.argtypes = [I, _pi, _pd, _pd, _pd, _pd, D, D, D, Lg, _pd]
+        L.or_eik_lf_point.restype = Lg
+        L.or_assemble_seeds.argtypes = [I, _pi, _pd, _pd, _pd, _pd, _pd, _pl, I, _pl, _pi, _pd, _pd, _pd, _pi]
+        L.or_assemble_seeds.restype = Lg
         _lib = L
     return _lib
 
@@ -171,8 +178,9 @@ class Tangent:
         return rem.astype(bool)
 
 
-def assemble(grid, G, T, s, src) -> Tangent:
-    """Sec. 3.1-3.2: upwind rows and calibration for one source state T."""
+def assemble(grid, G, T, s, src, seeds=None) -> Tangent:
+    """Sec. 3.1-3.2: upwind rows and calibration for one source state T.  The seed rows
+    (identities) are the source node, or the given seed nodes of a point source."""
     n, dxi = _n(grid)
     N = grid.N
     gT = grad(grid, T)
@@ -183,9 +191,16 @@ def assemble(grid, G, T, s, src) -> Tangent:
     w = np.zeros(cap)
     cs = np.zeros(N)
     rt = np.zeros(N, dtype=np.int32)
-    nnz = lib().or_assemble(grid.ndim, n, dxi, np.ascontiguousarray(G.reshape(-1)), gT.reshape(-1),
-                            np.ascontiguousarray(T, dtype=np.float64), np.ascontiguousarray(s, dtype=np.float64),
-                            int(src), row_ptr, col, cw, w, cs, rt)
+    if seeds is None:
+        nnz = lib().or_assemble(grid.ndim, n, dxi, np.ascontiguousarray(G.reshape(-1)), gT.reshape(-1),
+                                np.ascontiguousarray(T, dtype=np.float64), np.ascontiguousarray(s, dtype=np.float64),
+                                int(src), row_ptr, col, cw, w, cs, rt)
+    else:
+        sd = np.ascontiguousarray(seeds, dtype=np.int64)
+        nnz = lib().or_assemble_seeds(grid.ndim, n, dxi, np.ascontiguousarray(G.reshape(-1)), gT.reshape(-1),
+                                      np.ascontiguousarray(T, dtype=np.float64),
+                                      np.ascontiguousarray(s, dtype=np.float64), sd, len(sd), row_ptr, col, cw, w,
+                                      cs, rt)
     if nnz < 0:
         raise ValueError("assembly failed")
     return Tangent(N, int(src), row_ptr, col[:nnz].copy(), cw[:nnz].copy(), w[:nnz].copy(), cs, rt)
@@ -260,6 +275,143 @@ def block_matrix(t: Tangent, nodes: np.ndarray) -> np.ndarray:
 
 def build_tangent(grid, G, T, s, src) -> Tangent:
     return condense(assemble(grid, G, T, s, src))
+
+
+# --------------------------------------------------------------------------- point sources
+@dataclass
+class PointSource:
+    """A source between grid nodes.  The paper supplies its source rows from a
+    differentiated source treatment (Sec. 3.1, 3.2) without printing it; reading:
+      * the source sits at fractional logical coordinates f; its cell has corner base
+        b_d = min(floor(f_d), n_d - 2) and local coordinates t = f - b; corner o (in the
+        order of itertools.product((0, 1), repeat=ndim)) has the multilinear weight
+        phi_o = prod_d (t_d if o_d else 1 - t_d), the product taken axis by axis;
+      * position x_src = sum_o phi_o x_o and slowness s_src = sum_o phi_o s_o, each summed
+        in corner order;
+      * the state is the factored solve with T0 = s_src |x - x_src|, every corner kept at
+        T = T0 (their distances r_o = |x_o - x_src|);
+      * the corners are the seed rows of A (identities), and differentiating T_o = s_src r_o
+        gives their right-hand side q_o = r_o sum_k phi_k ds_k."""
+    f: np.ndarray
+    nodes: np.ndarray
+    phi: np.ndarray
+    x: np.ndarray
+    s_src: float
+    r: np.ndarray
+
+
+def _cell(grid, f):
+    import itertools
+    nd = grid.ndim
+    n = [int(v) for v in grid.n[:nd]]
+    f = [float(v) for v in f]
+    base = [min(int(np.floor(f[d])), n[d] - 2) for d in range(nd)]
+    t = [f[d] - base[d] for d in range(nd)]
+    nodes, phi = [], []
+    for o in itertools.product((0, 1), repeat=nd):
+        idx = [base[d] + o[d] for d in range(nd)]
+        node = 0
+        for d in range(nd):
+            node = node * n[d] + idx[d]
+        w = 1.0
+        for d in range(nd):
+            w = w * (t[d] if o[d] else 1.0 - t[d])
+        nodes.append(node)
+        phi.append(w)
+    return np.array(nodes, dtype=np.int64), np.array(phi), tuple(base)
+
+
+def point_source(grid, s, f) -> PointSource:
+    nd = grid.ndim
+    for d in range(nd):
+        if not (0.0 <= float(f[d]) <= grid.n[d] - 1):
+            raise ValueError("source coordinate out of the grid")
+    nodes, phi, _ = _cell(grid, f)
+    x = np.zeros(nd)
+    s_src = 0.0
+    for k in range(len(nodes)):
+        for c in range(nd):
+            x[c] = x[c] + phi[k] * grid.xyz[nodes[k], c]
+        s_src = s_src + phi[k] * float(s[nodes[k]])
+    r = np.zeros(len(nodes))
+    for k in range(len(nodes)):
+        acc = 0.0
+        for c in range(nd):
+            d = grid.xyz[nodes[k], c] - x[c]
+            acc = acc + d * d
+        r[k] = np.sqrt(acc)
+    return PointSource(np.asarray(f, dtype=np.float64), nodes, phi, x, s_src, r)
+
+
+def eik_forward_point(grid, s, f, radius=1.0, tol=1e-12, max_cycles=2000):
+    """The factored state of a point source (PointSource's reading).  Nodes within
+    max(radius x largest spacing, largest corner distance) of x_src keep tau = 1, so
+    every seed corner holds T = s_src r exactly.  Returns (T [N], cycles, PointSource)."""
+    ps = point_source(grid, s, f)
+    n, dxi = _n(grid)
+    rad = max(float(radius) * max(grid.dxi), float(ps.r.max()))
+    T = np.zeros(grid.N)
+    cyc = lib().or_eik_lf_point(grid.ndim, n, dxi, np.ascontiguousarray(grid.xyz),
+                                np.ascontiguousarray(s, dtype=np.float64), np.ascontiguousarray(ps.x),
+                                float(ps.s_src), rad, float(tol), int(max_cycles), T)
+    return T, int(cyc), ps
+
+
+def build_tangent_point(grid, G, T, s, ps: PointSource) -> Tangent:
+    """The tangent of a point source: its cell corners are the seed rows."""
+    t = condense(assemble(grid, G, T, s, -1, seeds=ps.nodes))
+    t.ps = ps
+    return t
+
+
+def source_rhs(t: Tangent, ds: np.ndarray) -> np.ndarray:
+    """q = C ds (Sec. 3.2): q_i = c_i ds_i off the seeds; on a point source's seed rows
+    q_o = r_o sum_k phi_k ds_k (differentiated source treatment).  ds [N, R]."""
+    q = t.cs[:, None] * ds
+    ps = getattr(t, "ps", None)
+    if ps is not None:
+        sigma = ps.phi @ ds[ps.nodes]
+        q[ps.nodes] += ps.r[:, None] * sigma[None, :]
+    return q
+
+
+def source_rhs_T(t: Tangent, lam: np.ndarray) -> np.ndarray:
+    """C^T lam, the transpose of source_rhs.  lam [N, R]."""
+    out = t.cs[:, None] * lam
+    ps = getattr(t, "ps", None)
+    if ps is not None:
+        tau = ps.r @ lam[ps.nodes]
+        out[ps.nodes] += ps.phi[:, None] * tau[None, :]
+    return out
+
+
+def direct_term(grid, ps: PointSource, f_rec: np.ndarray):
+    """D_a of Eq. (source-jacobian) for off-grid receivers (reading): a receiver in the
+    source's cell is predicted by the source treatment itself, T_r = s_src |x_r - x_src|
+    (x_r the multilinear image of its fractional coordinates), so its row of D is
+    |x_r - x_src| phi (on the corners) and its row of P is zero; every other receiver has
+    a zero row of D.  Returns (D as CSR [n_rec, N], boolean mask of the direct receivers)."""
+    import scipy.sparse as sp
+    f_rec = np.asarray(f_rec, dtype=np.float64)
+    _, _, sbase = _cell(grid, ps.f)
+    rows, cols, vals = [], [], []
+    direct = np.zeros(len(f_rec), dtype=bool)
+    for j, fr in enumerate(f_rec):
+        nodes, phi, base = _cell(grid, fr)
+        if base != sbase:
+            continue
+        direct[j] = True
+        xr = np.zeros(grid.ndim)
+        for k in range(len(nodes)):
+            for c in range(grid.ndim):
+                xr[c] = xr[c] + phi[k] * grid.xyz[nodes[k], c]
+        rho = float(np.sqrt(np.sum((xr - ps.x) ** 2)))
+        for k in range(len(ps.nodes)):
+            rows.append(j)
+            cols.append(int(ps.nodes[k]))
+            vals.append(rho * ps.phi[k])
+    D = sp.csr_matrix((vals, (rows, cols)), shape=(len(f_rec), grid.N))
+    return D, direct
 
 
 # --------------------------------------------------------------------------- solves
@@ -345,8 +497,7 @@ def J(tans, s, rec, p, model=MODEL_SLOWNESS, shared=True, solver=solve):
         pa = p if shared else p[a]
         pa = pa if pa.ndim == 2 else pa[:, None]
         ds = m[:, None] * pa
-        q = t.cs[:, None] * ds
-        dT = solver(t, q)
+        dT = solver(t, source_rhs(t, ds))
         out.append(dT[np.asarray(rec)])
     return np.stack(out)
 
@@ -360,7 +511,7 @@ def JT(tans, s, rec, y, model=MODEL_SLOWNESS, sum_sources=True, solver=solve_T):
         r = np.zeros((t.N, y.shape[2]))
         np.add.at(r, np.asarray(rec), y[a])
         lam = solver(t, r)
-        outs.append(m[:, None] * t.cs[:, None] * lam)
+        outs.append(m[:, None] * source_rhs_T(t, lam))
     outs = np.stack(outs)
     return outs.sum(axis=0) if sum_sources else outs
 
@@ -575,22 +726,28 @@ def receiver_interp(grid, f: np.ndarray):
                          shape=(len(f), int(np.prod(n))))
 
 
-def J_interp(tans, s, Ps, p, model=MODEL_SLOWNESS):
-    """J_a p = P_a A_a^-1 C_a M p with a sparse P_a per source (D = 0); p [N, R] shared.
-    Returns [S, n_rec, R]."""
+def J_interp(tans, s, Ps, p, model=MODEL_SLOWNESS, Ds=None):
+    """Eq. (source-jacobian): J_a p = (P_a A_a^-1 C_a + D_a) M p with a sparse P_a per
+    source (D_a = 0 unless given); p [N, R] shared.  Returns [S, n_rec, R]."""
     m = model_factor(s, model)
     out = []
-    for t, P in zip(tans, Ps):
-        dT = solve(t, t.cs[:, None] * (m[:, None] * p))
-        out.append(P @ dT)
+    for a, (t, P) in enumerate(zip(tans, Ps)):
+        ds = m[:, None] * p
+        d = P @ solve(t, source_rhs(t, ds))
+        if Ds is not None and Ds[a] is not None:
+            d = d + Ds[a] @ ds
+        out.append(d)
     return np.stack(out)
 
 
-def JT_interp(tans, s, Ps, y, model=MODEL_SLOWNESS):
-    """sum_a M^T C^T A_a^-T P_a^T y_a; y [S, n_rec, R].  Returns [N, R]."""
+def JT_interp(tans, s, Ps, y, model=MODEL_SLOWNESS, Ds=None):
+    """Eq. (source-transpose) summed over sources: sum_a M^T (C_a^T A_a^-T P_a^T y_a +
+    D_a^T y_a); y [S, n_rec, R].  Returns [N, R]."""
     m = model_factor(s, model)
     g = 0.0
     for a, (t, P) in enumerate(zip(tans, Ps)):
-        lam = solve_T(t, P.T @ y[a])
-        g = g + m[:, None] * t.cs[:, None] * lam
+        h = source_rhs_T(t, solve_T(t, P.T @ y[a]))
+        if Ds is not None and Ds[a] is not None:
+            h = h + Ds[a].T @ y[a]
+        g = g + m[:, None] * h
     return g

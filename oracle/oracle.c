@@ -132,10 +132,30 @@ int or_grad(int ndim, const int *n, const double *dxi, const double *f, double *
 /* row_type: 0 interior, 1 seed, 2 identity (no upstream).                    */
 /* Returns nnz, or -1 on bad input.                                           */
 /* ------------------------------------------------------------------------ */
+static int in_list(long i, const long *list, int n)
+{
+    for (int k = 0; k < n; ++k)
+        if (list[k] == i) return 1;
+    return 0;
+}
+
+/* The same rows with a set of seed rows (an on-grid source: its node; an off-grid point */
+/* source: the corners of its cell).                                                     */
+long or_assemble_seeds(int ndim, const int *n, const double *dxi, const double *G, const double *gradT,
+                       const double *T, const double *s, const long *seeds, int nseeds,
+                       long *row_ptr, int *col, double *cw, double *w, double *cs, int *row_type);
+
 long or_assemble(int ndim, const int *n, const double *dxi, const double *G, const double *gradT,
                  const double *T, const double *s, long src,
                  long *row_ptr /* [N+1] */, int *col /* [2 ndim N] */, double *cw /* c_ij */,
                  double *w, double *cs /* [N] */, int *row_type /* [N] */)
+{
+    return or_assemble_seeds(ndim, n, dxi, G, gradT, T, s, &src, 1, row_ptr, col, cw, w, cs, row_type);
+}
+
+long or_assemble_seeds(int ndim, const int *n, const double *dxi, const double *G, const double *gradT,
+                       const double *T, const double *s, const long *seeds, int nseeds,
+                       long *row_ptr, int *col, double *cw, double *w, double *cs, int *row_type)
 {
     long st[3], N = 1, nnz = 0;
     int idx[3];
@@ -145,7 +165,7 @@ long or_assemble(int ndim, const int *n, const double *dxi, const double *G, con
     for (long i = 0; i < N; ++i) {
         row_ptr[i] = nnz;
         coords(ndim, n, i, idx);
-        if (i == src) { row_type[i] = 1; cs[i] = 0.0; continue; }
+        if (in_list(i, seeds, nseeds)) { row_type[i] = 1; cs[i] = 0.0; continue; }
         long start = nnz;
         for (int d = 0; d < ndim; ++d) {
             for (int sg = -1; sg <= 1; sg += 2) {
@@ -540,8 +560,28 @@ long or_kahn_residual(long N, const long *row_ptr, const int *col, char *removed
 /* this keeps the iteration monotone.  Start tau = 1; stop when the largest  */
 /* change over one cycle is below tol.  Writes T [N]; returns cycles or -1.  */
 /* ------------------------------------------------------------------------ */
+static long eik_lf_core(int ndim, const int *n, const double *dxi, const double *xyz, const double *s,
+                        const double *xsrc, double ss, double radius, double tol, long max_cycles, double *T);
+
 long or_eik_lf(int ndim, const int *n, const double *dxi, const double *xyz, const double *s, long src,
                double radius, double tol, long max_cycles, double *T)
+{
+    long N = 1;
+    for (int d = 0; d < ndim; ++d) N *= n[d];
+    if (src < 0 || src >= N) return -2;
+    return eik_lf_core(ndim, n, dxi, xyz, s, xyz + src * ndim, s[src], radius, tol, max_cycles, T);
+}
+
+/* The same solve for a source at a point x_src between nodes with slowness s_src there: */
+/* T0 = s_src |x - x_src|, nodes within radius of x_src keep tau = 1.                    */
+long or_eik_lf_point(int ndim, const int *n, const double *dxi, const double *xyz, const double *s,
+                     const double *xsrc, double ssrc, double radius, double tol, long max_cycles, double *T)
+{
+    return eik_lf_core(ndim, n, dxi, xyz, s, xsrc, ssrc, radius, tol, max_cycles, T);
+}
+
+static long eik_lf_core(int ndim, const int *n, const double *dxi, const double *xyz, const double *s,
+                        const double *xsrc, double ss, double radius, double tol, long max_cycles, double *T)
 {
     long st[3], N = 1;
     int idx[3];
@@ -553,10 +593,9 @@ long or_eik_lf(int ndim, const int *n, const double *dxi, const double *xyz, con
     double *alpha = malloc(N * ndim * sizeof(double)), *tau = malloc(N * sizeof(double));
     char *fixed = malloc(N);
     or_metric(ndim, n, dxi, xyz, Jm, G, NULL);
-    double ss = s[src];
     for (long i = 0; i < N; ++i) {
         double dd[3], r2 = 0.0;
-        for (int c = 0; c < ndim; ++c) { dd[c] = xyz[i * ndim + c] - xyz[src * ndim + c]; r2 = r2 + dd[c] * dd[c]; }
+        for (int c = 0; c < ndim; ++c) { dd[c] = xyz[i * ndim + c] - xsrc[c]; r2 = r2 + dd[c] * dd[c]; }
         double r = sqrt(r2);
         T0[i] = ss * r;
         double gx[3];
