@@ -181,6 +181,22 @@ int eik_forward(const eik_grid *g, const double *s, int S, const int *src_node,
 int eik_forward_noalloc(const eik_grid *g, const double *s, int S, const int *src_node,
                         double *T, const eik_opts *opts, int *cycles, eik_stream stream);
 
+/*
+ * eik_forward_points -- the state solve of eik_forward for point sources between grid
+ * nodes (the off-grid sources of Sec. 3.1 / 4.4; the paper gives the source treatment no
+ * formula).  Reading: source a sits at fractional logical coordinates f[a] (0 <= f_d <=
+ * n_d - 1); its cell has corner base b_d = min(floor(f_d), n_d - 2) and the corners the
+ * multilinear weights phi_q of f; the source position is x_src = sum_q phi_q x_q and its
+ * slowness s_src = sum_q phi_q s_q (corner q: axis 0 the most significant bit).  The
+ * factored solve uses T0 = s_src |x - x_src|; nodes within max(eik_src_radius x largest
+ * spacing, largest corner distance) of x_src keep tau = 1, so every corner holds
+ * T = s_src |x_q - x_src|.
+ *   src_f    host [S][ndim] fractional logical coordinates of the sources
+ *   T        device [S][N] output; other arguments and errors as eik_forward
+ */
+int eik_forward_points(const eik_grid *g, const double *s, int S, const double *src_f,
+                       double *T, const eik_opts *opts, int *cycles, eik_stream stream);
+
 /* Bytes of the fixed scratch array behind eik_forward_noalloc. */
 size_t eik_forward_noalloc_capacity(void);
 
@@ -205,6 +221,26 @@ typedef struct eik_tangent eik_tangent;
 int tangent_build(const eik_grid *g, const double *T, const double *s, int S,
                   const int *src_node, const int *rec_node, int n_rec,
                   const eik_opts *opts, eik_tangent **out, eik_stream stream);
+
+/*
+ * tangent_build_points -- tangent_build for point sources (eik_forward_points' reading):
+ * the seed rows of source a are the 2^ndim corners of its cell (identities), with the
+ * differentiated source treatment as their right-hand side, q_q = r_q sum_k phi_k ds_k
+ * (r_q = |x_q - x_src|, ds = M p).  Every Jacobian call of the tangent includes these
+ * rows; an off-grid receiver set later with tangent_set_receivers that lies in its
+ * source's cell is carried by the direct term D_a of Eq. (source-jacobian):
+ * d_rec = |x_r - x_src| sum_k phi_k ds_k, with a zero row of P.  The build also forms
+ * z_a = A_a^-1 e_a (e_a = r on the seed rows; FP64 [S][N], one extra traversal), so J p
+ * adds sigma_a z_a at the outputs (sigma_a = sum_k phi_k ds_k) and J^T y adds
+ * M^T Phi^T sum_q r_q lam_q in source order.
+ *   src_f    host [S][ndim] fractional logical coordinates (as eik_forward_points)
+ *   T        device [S][N] states of these sources (e.g. from eik_forward_points)
+ * Other arguments, ownership and errors as tangent_build.  The batched applies
+ * (tangent_apply_batch, tangent_apply_T_batch) reject point-source tangents.
+ */
+int tangent_build_points(const eik_grid *g, const double *T, const double *s, int S,
+                         const double *src_f, const int *rec_node, int n_rec,
+                         const eik_opts *opts, eik_tangent **out, eik_stream stream);
 
 /*
  * tangent_apply -- J p for all sources (Sec. 4.4, Eq. source-jacobian, D = 0;

@@ -23,7 +23,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libeik.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NO_FMAD = {"eik_setup.cu", "eik_forward.cu"}
+NO_FMAD = {"eik_setup.cu", "eik_forward.cu", "eik_points.cu"}
 
 
 def nvcc() -> str:

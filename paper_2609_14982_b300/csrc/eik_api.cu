@@ -78,6 +78,29 @@ int tangent_build(const eik_grid *g, const double *T, const double *s, int S, co
     })
 }
 
+int tangent_build_points(const eik_grid *g, const double *T, const double *s, int S, const double *src_f,
+                         const int *rec_node, int n_rec, const eik_opts *opts, eik_tangent **out, eik_stream stream)
+{
+    EIK_GUARD({
+        if (!out) { eik::set_error("out is NULL"); return EIK_ERR_INVALID; }
+        *out = nullptr;
+        int rc = check_grid(g);
+        if (rc) return rc;
+        if (S <= 0 || !T || !s || !src_f || n_rec < 0 || (n_rec > 0 && !rec_node)) {
+            eik::set_error("bad tangent_build_points arguments");
+            return EIK_ERR_INVALID;
+        }
+        eik_opts def;
+        eik_opts_default(&def);
+        Tangent *t = nullptr;
+        rc = eik::build_tangent(g, T, s, S, nullptr, rec_node, n_rec, opts ? opts : &def, &t, (cudaStream_t)stream,
+                                src_f);
+        if (rc) return rc;
+        *out = new eik_tangent{t};
+        return EIK_OK;
+    })
+}
+
 int tangent_apply(eik_tangent *t, const void *p, int shared_model, int R, void *dT_full, void *d_rec, int dtype,
                   eik_stream stream)
 {

@@ -1930,8 +1930,20 @@ int traverse(Tangent *t, bool TR, int mode, const void *in, int shared_in, int R
         if (dtype == EIK_F32) rc = TR ? dispatch_v<float, true>(t, P, st) : dispatch_v<float, false>(t, P, st);
         else rc = TR ? dispatch_v<double, true>(t, P, st) : dispatch_v<double, false>(t, P, st);
         if (rc) return rc;
+        if (!TR && mode == MODE_J && t->pts.K > 0) {
+            // point sources: the seed rows' share sigma_a z_a (linear in the model input)
+            rc = seed_sigma(t, inp, shared_in, (long long)R, w, dtype, st);
+            if (!rc && auxp && t->n_rec > 0) rc = seed_add(t, t->n_rec, w, t->pts.zrec, auxp, (long long)R, dtype, st);
+            if (!rc && outp) rc = seed_add(t, t->N, w, t->pts.z, outp, (long long)R, dtype, st);
+            if (rc) return rc;
+        }
         if (TR && mode == MODE_J && sum_sources && out_aux) {
             rc = source_sum(t, w, auxp, (long long)R, dtype, st, sum_sources == 2);
+            if (rc) return rc;
+        }
+        if (TR && mode == MODE_J && t->pts.K > 0 && out_aux) {
+            // point sources: M^T Phi^T sum_q r_q lam_q, added in source order
+            rc = seed_scatter(t, w, auxp, (long long)R, sum_sources == 0, nullptr, 0, 0, nullptr, dtype, st);
             if (rc) return rc;
         }
     }
@@ -1976,6 +1988,8 @@ static int launch_batch(Tangent *const *ts, int ntan, const TravParams *Ps, cons
 int traverse_batch(Tangent *const *ts, int ntan, bool TR, const void *const *in, const int *R, void *const *out,
                    int dtype, cudaStream_t st)
 {
+    for (int k = 0; k < ntan; ++k)
+        if (ts[k] && ts[k]->pts.K > 0) { set_error("batched applies take tangents of node sources only"); return EIK_ERR_INVALID; }
     if (ntan < 1 || ntan > CL_MAXTAN) { set_error("batch: 1..%d tangents", CL_MAXTAN); return EIK_ERR_INVALID; }
     if (dtype != EIK_F32 && dtype != EIK_F64) { set_error("bad dtype"); return EIK_ERR_INVALID; }
     const size_t esz = dtype == EIK_F32 ? 4 : 8;

@@ -61,6 +61,46 @@ __global__ void k_eik_prep(GridDesc g, int S, const double *__restrict__ xyz, co
     tau[v] = 1.0;
 }
 
+// the same for point sources: position xs [S][3], slowness ss [S] and fixed radius rad [S]
+// per source (the point-source reading: every corner of the source cell stays fixed)
+__global__ void k_eik_prep_pt(GridDesc g, int S, const double *__restrict__ xyz, const double *__restrict__ Jm,
+                              const double *__restrict__ G, const double *__restrict__ xs, const double *__restrict__ ss,
+                              const double *__restrict__ rad, double *T0, double *g0, double *alpha,
+                              unsigned char *fixed, double *tau)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= g.N * S) return;
+    const int nd = g.ndim;
+    long long i = v / S, a = v - i * S;
+    const double sv = ss[a];
+    double d[3], r2 = 0.0;
+    for (int c = 0; c < nd; ++c) { d[c] = xyz[i * nd + c] - xs[a * 3 + c]; r2 = r2 + d[c] * d[c]; }
+    double r = sqrt(r2);
+    T0[v] = sv * r;
+    double gx[3];
+    for (int c = 0; c < nd; ++c) gx[c] = r > 0.0 ? sv * d[c] / r : 0.0;
+    for (int b = 0; b < nd; ++b) {
+        double acc = 0.0;
+        for (int c = 0; c < nd; ++c) acc = acc + Jm[i * nd * nd + c * nd + b] * gx[c];
+        g0[v * nd + b] = acc;
+    }
+    for (int b = 0; b < nd; ++b) alpha[v * nd + b] = T0[v] * sqrt(G[i * nd * nd + b * nd + b]);
+    fixed[v] = r <= rad[a] ? 1 : 0;
+    tau[v] = 1.0;
+}
+
+// fixed radius per point source: max(radius, largest corner distance); FP64 threshold
+__global__ void k_point_radius(int S, const double *__restrict__ r, const double *__restrict__ ss, double radius,
+                               double dist64, double *__restrict__ rad, double *__restrict__ t0_fp64)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= S) return;
+    double m = radius;
+    for (int q = 0; q < 8; ++q) m = r[a * 8 + q] > m ? r[a * 8 + q] : m;
+    rad[a] = m;
+    t0_fp64[a] = ss[a] * dist64;
+}
+
 struct LFParams {
     GridDesc g;
     int S, order, h, lo0, hi0;
@@ -336,11 +376,13 @@ static cudaError_t lf_cycles(LFParams P, int S, long long SN, int m0, int m1, in
 
 using namespace eik;
 
-extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const int *src_node, double *T,
-                           const eik_opts *opts_in, int *cycles, eik_stream stream)
+// node sources (src_node) or point sources (src_f: host [S][ndim] fractional logical
+// coordinates)
+static int forward_impl(const eik_grid *gin, const double *s, int S, const int *src_node, const double *src_f,
+                        double *T, const eik_opts *opts_in, int *cycles, eik_stream stream)
 {
     try {
-        if (!gin || (gin->ndim != 2 && gin->ndim != 3) || !gin->xyz || !s || !T || !src_node || S <= 0) {
+        if (!gin || (gin->ndim != 2 && gin->ndim != 3) || !gin->xyz || !s || !T || (!src_node && !src_f) || S <= 0) {
             set_error("bad eik_forward arguments");
             return EIK_ERR_INVALID;
         }
@@ -350,8 +392,9 @@ extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const in
         GridDesc g = make_grid_desc(gin);
         for (int d = 0; d < g.ndim; ++d)
             if (g.n[d] < 3) { set_error("grid needs >= 3 nodes per axis"); return EIK_ERR_INVALID; }
-        for (int a = 0; a < S; ++a)
-            if (src_node[a] < 0 || src_node[a] >= g.N) { set_error("source node out of range"); return EIK_ERR_INVALID; }
+        if (src_node)
+            for (int a = 0; a < S; ++a)
+                if (src_node[a] < 0 || src_node[a] >= g.N) { set_error("source node out of range"); return EIK_ERR_INVALID; }
         cudaStream_t st = (cudaStream_t)stream;
         const int nd = g.ndim;
         const long long N = g.N, SN = N * S;
@@ -359,11 +402,17 @@ extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const in
         unsigned char *fixed = nullptr, *active = nullptr;
         int *src_d = nullptr;
         unsigned long long *dmax = nullptr;
-        double *t0_fp64 = nullptr;
+        double *t0_fp64 = nullptr, *rad = nullptr;
+        PointData pd;
         auto release = [&]() {
             cudaFree(G); cudaFree(Jm); cudaFree(T0); cudaFree(g0); cudaFree(alpha); cudaFree(tau);
-            cudaFree(fixed); cudaFree(active); cudaFree(src_d); cudaFree(dmax); cudaFree(t0_fp64);
+            cudaFree(fixed); cudaFree(active); cudaFree(src_d); cudaFree(dmax); cudaFree(t0_fp64); cudaFree(rad);
+            free_point_data(pd);
         };
+        if (src_f) {
+            int rc = point_sources(g, gin->xyz, s, S, src_f, pd, st);
+            if (rc) { release(); return rc; }
+        }
 #define TRY(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { int rc_ = cuda_fail(e_, #call, __FILE__, __LINE__); release(); return rc_; } } while (0)
         TRY(cudaMalloc(&G, N * nd * nd * sizeof(double)));
         TRY(cudaMalloc(&Jm, N * nd * nd * sizeof(double)));
@@ -376,18 +425,26 @@ extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const in
         TRY(cudaMalloc(&dmax, (size_t)S * DSLOTS * sizeof(unsigned long long)));
         TRY(cudaMalloc(&active, S));
         TRY(cudaMalloc(&t0_fp64, S * sizeof(double)));
-        TRY(cudaMemcpyAsync(src_d, src_node, S * sizeof(int), cudaMemcpyHostToDevice, st));
         double hmax = 0.0;
         for (int d = 0; d < nd; ++d) hmax = std::max(hmax, g.dxi[d]);
         k_metric<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(g, gin->xyz, G, Jm);
-        k_eik_prep<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(g, S, gin->xyz, Jm, G, s, src_d,
-                                                                  opts->eik_src_radius * hmax, T0, g0, alpha, fixed, tau);
+        if (src_f) {
+            TRY(cudaMalloc(&rad, S * sizeof(double)));
+            k_point_radius<<<(S + 127) / 128, 128, 0, st>>>(S, pd.r, pd.ss, opts->eik_src_radius * hmax,
+                                                            opts->eik_fp64_radius * hmax, rad, t0_fp64);
+            k_eik_prep_pt<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(g, S, gin->xyz, Jm, G, pd.xs, pd.ss, rad, T0,
+                                                                         g0, alpha, fixed, tau);
+        } else {
+            TRY(cudaMemcpyAsync(src_d, src_node, S * sizeof(int), cudaMemcpyHostToDevice, st));
+            k_eik_prep<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(g, S, gin->xyz, Jm, G, s, src_d,
+                                                                      opts->eik_src_radius * hmax, T0, g0, alpha, fixed, tau);
+            k_t0_threshold<<<(S + 127) / 128, 128, 0, st>>>(S, s, src_d, opts->eik_fp64_radius * hmax, t0_fp64);
+        }
         TRY(cudaGetLastError());
         LFParams P{};
         P.g = g; P.S = S; P.G = G; P.s = s; P.T0 = T0; P.g0 = g0; P.alpha = alpha; P.fixed = fixed; P.tau = tau;
         P.dmax = dmax; P.active = active;
         P.fp32 = opts->eik_fp32 ? 1 : 0; P.t0_fp64 = t0_fp64;
-        k_t0_threshold<<<(S + 127) / 128, 128, 0, st>>>(S, s, src_d, opts->eik_fp64_radius * hmax, t0_fp64);
         const double tol = opts->eik_fp32 ? std::max(opts->eik_tol, 1e-6) : opts->eik_tol;
         const int m0 = g.n[0] - 2, m1 = g.n[1] - 2, m2 = nd == 3 ? g.n[2] - 2 : 1;
         const int hmax_i = (m0 - 1) + (m1 - 1) + (nd == 3 ? m2 - 1 : 0);
@@ -407,6 +464,20 @@ extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const in
         set_error("eik_forward failed");
         return EIK_ERR_INVALID;
     }
+}
+
+extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const int *src_node, double *T,
+                           const eik_opts *opts_in, int *cycles, eik_stream stream)
+{
+    if (!src_node) { set_error("bad eik_forward arguments"); return EIK_ERR_INVALID; }
+    return forward_impl(gin, s, S, src_node, nullptr, T, opts_in, cycles, stream);
+}
+
+extern "C" int eik_forward_points(const eik_grid *gin, const double *s, int S, const double *src_f, double *T,
+                                  const eik_opts *opts_in, int *cycles, eik_stream stream)
+{
+    if (!src_f) { set_error("bad eik_forward_points arguments"); return EIK_ERR_INVALID; }
+    return forward_impl(gin, s, S, nullptr, src_f, T, opts_in, cycles, stream);
 }
 
 // ---------------------------------------------------------------------------------

@@ -55,6 +55,28 @@ struct Block {
     long long ws;   // offset (in rows) of the block's rows in the workspace
 };
 
+// Off-grid point sources (see eik_points.cu): per source the 2^ndim corners of its cell
+// (arrays padded to 8 corners), all device [S][.] unless noted.
+struct PointData {
+    int S = 0, K = 0;              // sources, corners per source (0: node sources)
+    double *f = nullptr;           // [S][3] fractional logical coordinates
+    int *node = nullptr;           // [S][8] corner nodes (-1 padding)
+    double *phi = nullptr;         // [S][8] multilinear weights
+    double *phim = nullptr;        // [S][8] phi x model factor at the corner
+    double *xs = nullptr;          // [S][3] source positions
+    double *ss = nullptr;          // [S] source slownesses
+    double *r = nullptr;           // [S][8] seed distances |x_q - x_src|
+    double *z = nullptr;           // [S][N] A^-1 e (e = r on the seed rows), natural order
+    double *zrec = nullptr;        // [S][n_rec] z at the on-grid receivers
+    double *sigma = nullptr;       // [S][sigma_cols] sum_q phim_q p_q of the current columns
+    int sigma_cols = 0;
+    double *ip_rho = nullptr;      // [S][n_ip] direct receivers: |x_r - x_src|, else -1
+    double *ip_zeta = nullptr;     // [S][n_ip] rho (direct) or P z
+    std::vector<int> base;         // host [S][3] cell base
+    std::vector<double> xs_host;   // host [S][3]
+    std::vector<double> corner_xyz;  // host [S][8][3] corner positions
+};
+
 struct Tangent {
     int S = 0;
     long long N = 0;
@@ -160,11 +182,29 @@ struct Tangent {
     void *sweep_w[4] = {nullptr, nullptr, nullptr, nullptr};
     unsigned int *sweep_flags = nullptr;
     std::map<std::vector<long long>, cudaGraphExec_t> sweep_graphs;
+    // off-grid point sources (tangent_build_points); pts.K == 0 for node sources
+    PointData pts;
 };
 
+// src_f (host [S][ndim] fractional logical coordinates) selects point sources; then
+// src_node is ignored
 int build_tangent(const eik_grid *g, const double *T, const double *s, int S, const int *src_node,
                   const int *rec_node, int n_rec, const eik_opts *opts, Tangent **out,
-                  cudaStream_t stream);
+                  cudaStream_t stream, const double *src_f = nullptr);
+
+// point sources: corners, weights, positions and seed distances (allocates pd's device
+// arrays; synchronizes); the tangent's model factors and z = A^-1 e after its build
+int point_sources(const GridDesc &g, const double *xyz, const double *s, int S, const double *f_host, PointData &pd,
+                  cudaStream_t st);
+void free_point_data(PointData &pd);
+int point_tangent_setup(Tangent *t, const double *s, cudaStream_t st);
+// J: sigma of the current columns from the model input; out[a][j][r] += sigma zeta[a][j]
+int seed_sigma(Tangent *t, const void *in, int shared_in, long long ld_in, int w, int dtype, cudaStream_t st);
+int seed_add(Tangent *t, long long n, int w, const double *zeta, void *out, long long ld, int dtype, cudaStream_t st);
+// J^T: g += M^T Phi^T (r . lam_seeds + rho . y_direct), in source order, from the workspace
+int seed_scatter(Tangent *t, int w, void *g, long long ld_g, bool per_source, const void *y, long long ld_y,
+                 int n_y, const double *rho, int dtype, cudaStream_t st);
+int seed_interp_setup(Tangent *t, const std::vector<double> &rho_host, cudaStream_t st);
 void free_tangent(Tangent *t);
 
 enum Mode : int { MODE_J = 0, MODE_RAW = 1 };

@@ -1,7 +1,8 @@
 // Off-grid receivers (Sec. 4.4's P_a for receivers between grid nodes): P_a samples the
 // transported field multilinearly at each receiver's fractional logical position (a
 // reading; the paper gives no formula), and P_a^T spreads receiver data onto the
-// 2^ndim corner nodes with the same weights.  D_a = 0 (on-grid sources).
+// 2^ndim corner nodes with the same weights.  D_a = 0 for node sources; for point
+// sources (eik_points.cu) a receiver in the source's cell is carried by D_a instead.
 //   J:   traverse (receivers not fused), then gather each receiver's corners from the
 //        canonical-order workspace through pos.
 //   J^T: build the dense reverse input P^T y (a gather over the receivers touching each
@@ -112,6 +113,10 @@ static int apply_interp(Tangent *t, const void *ds, int shared, int R, void *d_r
                                                                     t->pos, (const T *)t->ws_vec,
                                                                     static_cast<T *>(d_rec) + r0, (long long)R);
         EIK_CHECK_LAUNCH();
+        if (t->pts.K > 0) {   // point sources: seed rows through z, and D for direct receivers
+            rc = seed_add(t, t->n_ip, w, t->pts.ip_zeta, static_cast<T *>(d_rec) + r0, (long long)R, dtype, st);
+            if (rc) return rc;
+        }
     }
     return EIK_OK;
 }
@@ -137,6 +142,11 @@ static int apply_interp_T(Tangent *t, const void *y, int R, void *g, int dtype, 
         if (rc) return rc;
         rc = source_sum(t, w, static_cast<T *>(g) + r0, (long long)R, dtype, st);
         if (rc) return rc;
+        if (t->pts.K > 0) {   // point sources: M^T Phi^T (r . lam_seeds + rho . y_direct)
+            rc = seed_scatter(t, w, static_cast<T *>(g) + r0, (long long)R, false, static_cast<const T *>(y) + r0,
+                              (long long)R, t->n_ip, t->pts.ip_rho, dtype, st);
+            if (rc) return rc;
+        }
     }
     return EIK_OK;
 }
@@ -152,6 +162,7 @@ int set_receivers_interp(Tangent *t, int n_rec, const double *f)
     const size_t ne = (size_t)S * n_rec * K;
     std::vector<int> node(ne);
     std::vector<double> wt(ne);
+    std::vector<double> rho((size_t)S * n_rec, -1.0);   // direct receivers of point sources
     long long stride[3] = {1, 1, 1};
     long long acc = 1;
     for (int d = nd - 1; d >= 0; --d) { stride[d] = acc; acc *= t->grid.n[d]; }
@@ -177,6 +188,25 @@ int set_receivers_interp(Tangent *t, int n_rec, const double *f)
             }
             node[q * K + c] = (int)j;
             wt[q * K + c] = wv;
+        }
+        if (t->pts.K > 0) {
+            // D_a: a receiver inside its source's cell takes the source treatment's value
+            // s_src |x_r - x_src| (its P row is zeroed); the corners of the two cells coincide
+            const size_t a = q / n_rec;
+            bool same = true;
+            for (int d = 0; d < nd; ++d) same = same && base[d] == t->pts.base[a * 3 + d];
+            if (same) {
+                double xr[3] = {0.0, 0.0, 0.0};
+                for (int c = 0; c < K; ++c)
+                    for (int d = 0; d < nd; ++d) xr[d] = xr[d] + wt[q * K + c] * t->pts.corner_xyz[(a * 8 + c) * 3 + d];
+                double acc = 0.0;
+                for (int d = 0; d < nd; ++d) {
+                    const double dd = xr[d] - t->pts.xs_host[a * 3 + d];
+                    acc = acc + dd * dd;
+                }
+                rho[q] = std::sqrt(acc);
+                for (int c = 0; c < K; ++c) wt[q * K + c] = 0.0;
+            }
         }
     }
     // P^T: per source, the touched nodes ascending and their corner entries
@@ -218,6 +248,7 @@ int set_receivers_interp(Tangent *t, int n_rec, const double *f)
     if (e != cudaSuccess) return cuda_fail(e, "tangent_set_receivers", __FILE__, __LINE__);
     t->n_ip = n_rec;
     t->n_ipt = n_ipt;
+    if (t->pts.K > 0) return seed_interp_setup(t, rho, nullptr);
     return EIK_OK;
 }
 

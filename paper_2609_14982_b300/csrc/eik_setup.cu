@@ -138,12 +138,13 @@ __global__ void k_grad(GridDesc g, int S, const double *__restrict__ T, double *
 // nodes, except the normal gradient component, which is the compact difference across
 // the face; a_f = sum_b Gf[d][b] gf[b]; j is upstream iff -side * a_f > 0, with
 // coupling c = -side * a_f / h_d.  Row: d_i = sum c, w = c / d_i; l_i = T_i - sum w T_j,
-// cs_i = l_i / s_i.  Seed rows (the source node) are identities with cs = 0; a non-seed
-// row without an upstream face is an identity with cs = T_i / s_i.
+// cs_i = l_i / s_i.  Seed rows (the source node, or the cell corners of a point source:
+// seeds [S][8], -1 padded) are identities with cs = 0; a non-seed row without an upstream
+// face is an identity with cs = T_i / s_i.
 // upmask bit (2 d + (side > 0)) marks an upstream face.
 // ---------------------------------------------------------------------------
 __global__ void k_assemble(GridDesc g, int S, const double *__restrict__ G, const double *__restrict__ gT,
-                           const double *__restrict__ T, const double *__restrict__ s, const int *__restrict__ src,
+                           const double *__restrict__ T, const double *__restrict__ s, const int *__restrict__ seeds,
                            int *__restrict__ cnt, int *__restrict__ nnode, double *__restrict__ nw,
                            unsigned char *__restrict__ upmask, double *__restrict__ cs,
                            unsigned long long *__restrict__ n_identity)
@@ -154,7 +155,9 @@ __global__ void k_assemble(GridDesc g, int S, const double *__restrict__ G, cons
     long long a = v / g.N, i = v - a * g.N;
     const double *Ta = T + a * g.N;
     const double *gTa = gT + a * g.N * nd;
-    if (i == src[a]) {
+    bool seed = false;
+    for (int q = 0; q < 8; ++q) seed = seed || seeds[a * 8 + q] == i;
+    if (seed) {
         cnt[v] = 0; upmask[v] = 0; cs[v] = 0.0;
         return;
     }
@@ -915,6 +918,7 @@ void free_tangent(Tangent *t)
                     t->ws_blk, t->ebase_d, t->tbase_d, t->ip_node, t->ip_w, t->ipt_node, t->ipt_ptr, t->ipt_e,
                     t->ws_in, t->lvl_d, t->blk_lvl_d, t->nlev_d, t->order_d};
     for (void *p : ptrs) if (p) cudaFree(p);
+    free_point_data(t->pts);
     if (t->params_d) cudaFree((void *)t->params_d);
     for (void *p : t->sweep_w) if (p) cudaFree(p);
     if (t->sweep_flags) cudaFree(t->sweep_flags);
@@ -925,15 +929,17 @@ void free_tangent(Tangent *t)
 }
 
 int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, const int *src_node,
-                  const int *rec_node, int n_rec, const eik_opts *opts, Tangent **out, cudaStream_t st)
+                  const int *rec_node, int n_rec, const eik_opts *opts, Tangent **out, cudaStream_t st,
+                  const double *src_f)
 {
     *out = nullptr;
     GridDesc g = make_grid_desc(gin);
     const long long N = g.N, SN = N * (long long)S;
     const int nd = g.ndim, slots = 2 * nd;
     if (SN >= (1ll << 31)) { set_error("sources x nodes = %lld; at most 2^31 - 1 supported", SN); return EIK_ERR_INVALID; }
-    for (int a = 0; a < S; ++a)
-        if (src_node[a] < 0 || src_node[a] >= N) { set_error("source %d node %d out of range", a, src_node[a]); return EIK_ERR_INVALID; }
+    if (!src_f)
+        for (int a = 0; a < S; ++a)
+            if (src_node[a] < 0 || src_node[a] >= N) { set_error("source %d node %d out of range", a, src_node[a]); return EIK_ERR_INVALID; }
 
     Tangent *t = new Tangent();
     t->S = S; t->N = N; t->n_rec = n_rec; t->grid = g; t->opts = *opts; t->model = opts->model;
@@ -953,7 +959,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
     TRY(sc.get(&fst, SN));
     TRY(sc.get(&bst, SN));
     TRY(sc.get(&flags, 8));
-    TRY(sc.get(&src_d, S));
+    TRY(sc.get(&src_d, (size_t)S * 8));
     TRY(sc.get(&nid, S));
     TRY(dalloc(&t->nrow_cnt, SN));
     TRY(dalloc(&t->nrow_node, SN * slots));
@@ -963,7 +969,17 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
     TRY(dalloc(&t->level, SN));
     cnt = t->nrow_cnt;
     lab = t->label;
-    TRY(cudaMemcpyAsync(src_d, src_node, S * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (src_f) {
+        // point sources: the seed rows are the corners of each source's cell
+        int rc = point_sources(g, gin->xyz, s, S, src_f, t->pts, st);
+        if (rc) return fail(rc);
+        TRY(cudaMemcpyAsync(src_d, t->pts.node, (size_t)S * 8 * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    } else {
+        std::vector<int> seeds((size_t)S * 8, -1);
+        for (int a = 0; a < S; ++a) seeds[(size_t)a * 8] = src_node[a];
+        TRY(cudaMemcpyAsync(src_d, seeds.data(), seeds.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        TRY(cudaStreamSynchronize(st));   // the host table goes out of scope
+    }
     TRY(cudaMemsetAsync(nid, 0, S * sizeof(unsigned long long), st));
 
     // ---- metric, gradient, rows (Sec. 2.2, 3.1, 3.2)
@@ -1480,6 +1496,12 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
     TRY(cudaGetLastError());
     TRY(cudaStreamSynchronize(st));
 #undef TRY
+    if (src_f) {
+        // point sources: model factors at the corners and z = A^-1 e (a traversal of the
+        // finished tangent)
+        int rc = point_tangent_setup(t, s, st);
+        if (rc) return fail(rc);
+    }
     *out = t;
     return EIK_OK;
 }

@@ -29,7 +29,7 @@ EXPORTED = ["eik_opts_default", "eik_last_error", "eik_version", "eik_forward", 
             "gn_create", "gn_dims", "gn_apply", "gn_apply_T", "gn_lsmr_start", "gn_lsmr_iterate",
             "gn_lsmr_solution", "gn_free", "model_cells_to_nodes", "model_nodes_to_cells",
             "tangent_set_receivers", "tangent_apply_interp", "tangent_apply_interp_T", "gn_create_cells", "gn_rhs",
-            "tangent_apply_batch", "tangent_apply_T_batch"]
+            "tangent_apply_batch", "tangent_apply_T_batch", "eik_forward_points", "tangent_build_points"]
 
 
 class EikError(RuntimeError):
@@ -78,6 +78,8 @@ def lib():
         L.eik_forward_noalloc.argtypes = [C.POINTER(Grid_), P, I, P, P, C.POINTER(Opts), C.POINTER(I), P]
         L.eik_forward_noalloc_capacity.restype = C.c_size_t
         L.tangent_build.argtypes = [C.POINTER(Grid_), P, P, I, P, P, I, C.POINTER(Opts), C.POINTER(P), P]
+        L.tangent_build_points.argtypes = [C.POINTER(Grid_), P, P, I, P, P, I, C.POINTER(Opts), C.POINTER(P), P]
+        L.eik_forward_points.argtypes = [C.POINTER(Grid_), P, I, P, P, C.POINTER(Opts), C.POINTER(I), P]
         L.tangent_apply.argtypes = [P, P, I, I, P, P, I, P]
         L.tangent_apply_T.argtypes = [P, P, I, I, P, P, I, P]
         L.tangent_solve.argtypes = [P, P, I, P, I, P]
@@ -226,6 +228,31 @@ def eik_forward(dgrid: DeviceGrid, s: torch.Tensor, src, opts: Opts | None = Non
     return out, cyc.value
 
 
+def _points(dgrid: DeviceGrid, src_f) -> torch.Tensor:
+    f = torch.as_tensor(src_f, dtype=torch.float64).cpu()
+    if f.dim() == 1:
+        f = f.unsqueeze(0)
+    if f.dim() != 2 or f.shape[1] != dgrid.c.ndim:
+        raise ValueError(f"point sources must be [S, {dgrid.c.ndim}] fractional logical coordinates")
+    return f.contiguous()
+
+
+def eik_forward_points(dgrid: DeviceGrid, s: torch.Tensor, src_f, opts: Opts | None = None,
+                       out: torch.Tensor | None = None):
+    """First-arrival traveltimes [S, N] (float64) for point sources at fractional logical
+    coordinates src_f [S, ndim]."""
+    f = _points(dgrid, src_f)
+    S = int(f.shape[0])
+    _check_state_args(dgrid, s, S, out)
+    if out is None:
+        out = torch.empty((S, dgrid.N), dtype=torch.float64, device=s.device)
+    cyc = C.c_int(0)
+    _check(lib().eik_forward_points(C.byref(dgrid.c), _dev(s, torch.float64, "s"), S, C.c_void_p(f.data_ptr()),
+                                    _dev(out, torch.float64, "T"), C.byref(opts) if opts else None, C.byref(cyc),
+                                    _stream()))
+    return out, cyc.value
+
+
 def eik_forward_noalloc(dgrid: DeviceGrid, s: torch.Tensor, src, out: torch.Tensor, opts: Opts | None = None):
     """Same result as eik_forward, without any device allocation inside the library: the
     caller provides T [S, N] (float64) and the scratch is the library's fixed array."""
@@ -241,9 +268,16 @@ def eik_forward_noalloc(dgrid: DeviceGrid, s: torch.Tensor, src, out: torch.Tens
 class Tangent:
     """The frozen per-source states S_a of all sources (owned by libeik)."""
 
-    def __init__(self, dgrid: DeviceGrid, T: torch.Tensor, s: torch.Tensor, src, rec=None, opts: Opts | None = None):
-        src = torch.as_tensor(src, dtype=torch.int32).contiguous().cpu()
-        self.S = int(src.numel())
+    def __init__(self, dgrid: DeviceGrid, T: torch.Tensor, s: torch.Tensor, src, rec=None, opts: Opts | None = None,
+                 points: bool = False):
+        """src: source nodes [S], or with points=True fractional logical coordinates [S, ndim]
+        of point sources (tangent_build_points)."""
+        if points:
+            src = _points(dgrid, src)
+            self.S = int(src.shape[0])
+        else:
+            src = torch.as_tensor(src, dtype=torch.int32).contiguous().cpu()
+            self.S = int(src.numel())
         if rec is None:
             rec = torch.zeros((self.S, 0), dtype=torch.int32)
         rec = torch.as_tensor(rec, dtype=torch.int32).cpu()
@@ -255,10 +289,11 @@ class Tangent:
         self.dgrid = dgrid
         self.opts = opts if opts is not None else default_opts()
         h = C.c_void_p()
-        _check(lib().tangent_build(C.byref(dgrid.c), _dev(T, torch.float64, "T"), _dev(s, torch.float64, "s"),
-                                   self.S, C.c_void_p(src.data_ptr()),
-                                   C.c_void_p(rec.data_ptr()) if self.n_rec else None, self.n_rec,
-                                   C.byref(self.opts), C.byref(h), _stream()))
+        build = lib().tangent_build_points if points else lib().tangent_build
+        _check(build(C.byref(dgrid.c), _dev(T, torch.float64, "T"), _dev(s, torch.float64, "s"),
+                     self.S, C.c_void_p(src.data_ptr()),
+                     C.c_void_p(rec.data_ptr()) if self.n_rec else None, self.n_rec,
+                     C.byref(self.opts), C.byref(h), _stream()))
         self.h = h
 
     def __del__(self):
