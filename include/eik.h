@@ -111,9 +111,10 @@ typedef struct {
     /* SCC block solves */
     int block_lu_min;          /* blocks of at least this many nodes are solved by FP64 forward and
                                   back substitution with their partial-pivot LU factors (one warp
-                                  per right-hand side); smaller blocks multiply by the explicit
-                                  inverse formed from the same factors (default 64; 0: always the
-                                  inverse) */
+                                  per right-hand side), the accuracy tier for ill-conditioned
+                                  blocks; other blocks multiply by the explicit inverse formed from
+                                  the same factors, which has the same FP64 work (k^2 per column)
+                                  and more parallelism (default 0: always the inverse) */
 } eik_opts;
 
 typedef struct {

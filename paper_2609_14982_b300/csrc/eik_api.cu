@@ -41,7 +41,7 @@ void eik_opts_default(eik_opts *o)
     o->eik_fp32 = 0;
     o->eik_fp64_radius = 8.0;
     o->item_deps = 1;
-    o->block_lu_min = 64;
+    o->block_lu_min = 0;
 }
 
 const char *eik_last_error(void) { return eik::last_error(); }

@@ -51,7 +51,7 @@ def test_version_and_defaults(libeik):
     assert b"sm_103a" in libeik.eik_version()
     o = eik.default_opts()
     assert o.schedule == eik.SCHED_PERSISTENT and o.wait_timeout_s > 0 and o.lu_pivot_tol > 0
-    assert o.block_lu_min == 64
+    assert o.block_lu_min == 0
 
 
 def test_binding_rejects_host_tensors():
