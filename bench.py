@@ -176,7 +176,9 @@ def run_ours(args):
              "cluster": eik.SCHED_CLUSTER}[args.schedule]
     opts = eik.default_opts(schedule=sched, item_deps=0 if args.level_waits else 1, ctas_per_sm=args.ctas_per_sm,
                             cluster_size=args.cluster_size, cluster_threads=args.cluster_threads,
-                            pass_units=args.pass_units)
+                            pass_units=args.pass_units, split_dirs=int(args.split_dirs))
+    if args.split_dirs and not args.ctas_per_sm:
+        opts.ctas_per_sm = 2
     if args.chunk:
         opts.chunk = args.chunk
     t0 = time.time()
@@ -194,7 +196,8 @@ def run_ours(args):
         rec = autotune(tan, R, dtype, reps=3, cache_path=None, cands=quick_candidates(R, dtype), seed=rank)
         tuned = {"setting": rec["setting"], "ms": round(rec["ms"], 3), "tune_s": round(rec["tune_s"], 2),
                  "tried": [{k: v for k, v in c.items() if k in ("ms", "schedule", "pass_units", "block_lu_min",
-                                                                 "cluster_size")} for c in rec["tried"]]}
+                                                                 "cluster_size", "split_dirs", "ctas_per_sm")}
+                           for c in rec["tried"]]}
         for c in tuned["tried"]:
             c["ms"] = round(c["ms"], 3)
         names = {eik.SCHED_PERSISTENT: "persistent", eik.SCHED_LEVELS: "levels", eik.SCHED_STAGED: "staged",
@@ -207,10 +210,39 @@ def run_ours(args):
     d_rec = torch.empty((S, n_rec, R), device=dev, dtype=dtype)
     gvec = torch.empty((N, R), device=dev, dtype=dtype)
     stream = torch.cuda.current_stream(dev)
+    # with split_dirs (chosen by the autotuner) J p and J^T y of a step run at once on two
+    # streams; the kernel times are then taken on those streams
+    concurrent = bool(tan.opts.split_dirs)
+    pair_streams = (torch.cuda.Stream(dev), torch.cuda.Stream(dev))
+
+    def pair(pv, yv, ev=None):
+        if not concurrent:
+            if ev: ev[0].record(stream)
+            tan.apply(pv, shared_model=True, d_rec=d_rec)
+            if ev: ev[1].record(stream)
+            tan.apply_T(yv, sum_sources=True, g=gvec)
+            if ev: ev[2].record(stream)
+            return
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        sa, sb = pair_streams
+        sa.wait_event(fork)
+        sb.wait_event(fork)
+        with torch.cuda.stream(sa):
+            if ev: ev[0].record(sa)
+            tan.apply(pv, shared_model=True, d_rec=d_rec)
+            if ev: ev[1].record(sa)
+        with torch.cuda.stream(sb):
+            if ev: ev[2].record(sb)
+            tan.apply_T(yv, sum_sources=True, g=gvec)
+            if ev: ev[3].record(sb)
+        for st_ in pair_streams:
+            join = torch.cuda.Event()
+            join.record(st_)
+            stream.wait_event(join)
 
     def step():
-        tan.apply(p, shared_model=True, d_rec=d_rec)
-        tan.apply_T(y, sum_sources=True, g=gvec)
+        pair(p, y)
         reduce_model_gradient(gvec)
 
     for _ in range(args.warmup):
@@ -218,8 +250,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     tan.status()
 
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for _ in range(args.steps)]
     clk = Clocks(torch.cuda.current_device())
     if world > 1:
         dist.barrier()
@@ -230,12 +261,7 @@ def run_ours(args):
     end = torch.cuda.Event(enable_timing=True)
     start.record(stream)
     for k in range(args.steps):
-        a, b, c = evs[k]
-        a.record(stream)
-        tan.apply(p, shared_model=True, d_rec=d_rec)
-        b.record(stream)
-        tan.apply_T(y, sum_sources=True, g=gvec)
-        c.record(stream)
+        pair(p, y, evs[k])
         reduce_model_gradient(gvec)
     end.record(stream)
     torch.cuda.synchronize()
@@ -244,8 +270,8 @@ def run_ours(args):
     clocks = clk.stop()
     tan.status()
     ms = start.elapsed_time(end) / args.steps
-    t_fwd = [a.elapsed_time(b) for a, b, _ in evs]
-    t_bwd = [b.elapsed_time(c) for _, b, c in evs]
+    t_fwd = [e[0].elapsed_time(e[1]) for e in evs]
+    t_bwd = [e[2].elapsed_time(e[3]) if concurrent else e[1].elapsed_time(e[2]) for e in evs]
     if world > 1:
         tt = torch.tensor([ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -264,8 +290,7 @@ def run_ours(args):
     def e2e_step():
         p_d.copy_(p_h, non_blocking=True)
         y_d.copy_(y_h, non_blocking=True)
-        tan.apply(p_d, shared_model=True, d_rec=d_rec)
-        tan.apply_T(y_d, sum_sources=True, g=gvec)
+        pair(p_d, y_d)
         reduce_model_gradient(gvec)
         drec_h.copy_(d_rec, non_blocking=True)
         g_h.copy_(gvec, non_blocking=True)
@@ -320,6 +345,8 @@ def run_ours(args):
                 "bytes_note": "p counted once per call; with p read once per source the update moves "
                               f"{ab['fwd_per_update_input_per_source']:.2f} B",
                 "peak_kind": f"{peak_kind} hbm_gbs",
+                "concurrent_with_other_direction": concurrent,
+                "pair_achieved_gbs": round((ab["fwd"] + ab["bwd"]) / (ms / 1e3) / 1e9, 1),
                 "other_direction": {"dir": other, "ms": round(mb, 4), "includes": "k_source_sum_vec",
                                     "frac": round(ab[other] / (mb / 1e3) / 1e9 / peak, 4)}}
 
@@ -357,6 +384,7 @@ def run_ours(args):
         "config": {"workload": workload, "grid": list(g.n), "nodes": N, "sources_per_gpu": S, "rhs": R,
                    "receivers": n_rec, "precision": "FP32 substitution, FP64 SCC blocks",
                    "schedule": schedule, "autotuned": tuned,
+                   "directions": "J p and J^T y concurrently on two streams (split_dirs)" if concurrent else "in order",
                    "waits": "levels" if args.level_waits else "items", "l2": "inputs larger than L2 (dT/lam 3.3 GB per direction)",
                    "parallelism": f"source-sharded x{world}" if world > 1 else "single GPU"},
         "roofline": roofline,
@@ -883,6 +911,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--schedule", choices=["persistent", "levels", "staged", "cluster"], default="persistent")
+    ap.add_argument("--split-dirs", action="store_true",
+                    help="run J p and J^T y of a step at once on two streams (2 CTAs per SM each unless given)")
     ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
                     help="pick the traversal setting by timing a short candidate list before the timed region")
     ap.add_argument("--cluster-size", type=int, default=0, help="cluster schedule: CTAs per cluster (0 = auto)")

@@ -115,6 +115,14 @@ typedef struct {
                                   blocks; other blocks multiply by the explicit inverse formed from
                                   the same factors, which has the same FP64 work (k^2 per column)
                                   and more parallelism (default 0: always the inverse) */
+    /* concurrency */
+    int split_dirs;            /* 1: the transpose direction keeps its own workspace, counters and
+                                  ticket, so tangent_apply and tangent_apply_T on one tangent may
+                                  run concurrently on two streams (give each about half the CTAs,
+                                  ctas_per_sm); costs one more [S][N][R] workspace.  The other
+                                  calls (interp forms, solves, sweeping) still must not overlap.
+                                  0 (default): calls on one tangent must not overlap on the
+                                  device */
 } eik_opts;
 
 typedef struct {
@@ -335,8 +343,9 @@ int tangent_status(eik_tangent *t, eik_stream stream);
 
 /*
  * tangent_tune -- replace the run-time options of a built tangent: schedule, ctas_per_sm,
- * rhs_chunk, wait_timeout_s and item_deps are taken from opts (structure options are
- * ignored).
+ * rhs_chunk, wait_timeout_s, item_deps, cluster_size, cluster_threads, pass_units,
+ * block_lu_min and split_dirs are taken from opts (structure options are ignored).
+ * Turning split_dirs on allocates the transpose's counters (synchronizes the device).
  * Used by the autotuner; affects later calls only.
  */
 int tangent_tune(eik_tangent *t, const eik_opts *opts);

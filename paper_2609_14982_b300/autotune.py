@@ -13,7 +13,9 @@ per (grid size, sources, levels, R, dtype) in a JSON file.  The knobs:
   block tiling       block_lu_min: SCC blocks of at least this size are solved by
                      column-parallel substitution with the LU factors instead of the
                      explicit inverse;
-  waits              per-item dependencies or whole previous level (persistent).
+  waits              per-item dependencies or whole previous level (persistent);
+  concurrency        split_dirs: J p and J^T y on two streams at once, each with about
+                     half the CTAs (the pair is timed that way).
 """
 from __future__ import annotations
 
@@ -26,6 +28,11 @@ import torch
 from . import eik
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "eik_autotune.json")
+
+
+# every knob at its default: a candidate names only what it changes
+DEFAULTS = {"schedule": eik.SCHED_PERSISTENT, "rhs_chunk": 0, "ctas_per_sm": 0, "item_deps": 1, "pass_units": 0,
+            "cluster_size": 0, "cluster_threads": 0, "block_lu_min": 0, "split_dirs": 0}
 
 
 def _key(tan, R: int, dtype) -> str:
@@ -54,6 +61,8 @@ def candidates(R: int, dtype) -> list:
                                 "cluster_threads": ct, "pass_units": pu})
         for blk in (0, 64):
             out.append({"schedule": eik.SCHED_PERSISTENT, "rhs_chunk": ch, "block_lu_min": blk})
+        for per_sm in (1, 2):
+            out.append({"schedule": eik.SCHED_PERSISTENT, "rhs_chunk": ch, "split_dirs": 1, "ctas_per_sm": per_sm})
     return out
 
 
@@ -62,8 +71,9 @@ def quick_candidates(R: int, dtype) -> list:
     each schedule, the cluster schedule at two sizes, and the lane-group and
     block-tiling variants of the persistent schedule."""
     base = {"rhs_chunk": 0, "ctas_per_sm": 0, "item_deps": 1, "pass_units": 0, "cluster_size": 0,
-            "cluster_threads": 0, "block_lu_min": 0}
+            "cluster_threads": 0, "block_lu_min": 0, "split_dirs": 0}
     out = [dict(base, schedule=eik.SCHED_PERSISTENT),
+           dict(base, schedule=eik.SCHED_PERSISTENT, split_dirs=1, ctas_per_sm=2),
            dict(base, schedule=eik.SCHED_PERSISTENT, pass_units=2),
            dict(base, schedule=eik.SCHED_PERSISTENT, block_lu_min=64),
            dict(base, schedule=eik.SCHED_CLUSTER),
@@ -72,16 +82,37 @@ def quick_candidates(R: int, dtype) -> list:
     return out
 
 
+def run_pair(tan, p, y, d_rec=None, g=None, streams=None):
+    """One J p + J^T y pair on the current stream: in order, or (split_dirs with two
+    streams given) J p on streams[0] and J^T y on streams[1] at once, joined back."""
+    if streams is None or not tan.opts.split_dirs:
+        tan.apply(p, shared_model=True, d_rec=d_rec)
+        tan.apply_T(y, sum_sources=True, g=g)
+        return
+    cur = torch.cuda.current_stream()
+    ev = torch.cuda.Event()
+    ev.record(cur)
+    for st in streams:
+        st.wait_event(ev)
+    with torch.cuda.stream(streams[0]):
+        tan.apply(p, shared_model=True, d_rec=d_rec)
+    with torch.cuda.stream(streams[1]):
+        tan.apply_T(y, sum_sources=True, g=g)
+    for st in streams:
+        done = torch.cuda.Event()
+        done.record(st)
+        cur.wait_event(done)
+
+
 def time_setting(tan, p, y, reps: int = 3) -> float:
     """Mean milliseconds of one J p + J^T y pair (after one untimed call)."""
-    tan.apply(p, shared_model=True)
-    tan.apply_T(y, sum_sources=True)
+    streams = (torch.cuda.Stream(), torch.cuda.Stream())
+    run_pair(tan, p, y, streams=streams)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(reps):
-        tan.apply(p, shared_model=True)
-        tan.apply_T(y, sum_sources=True)
+        run_pair(tan, p, y, streams=streams)
     e1.record(stream)
     torch.cuda.synchronize()
     tan.status()
@@ -101,7 +132,7 @@ def autotune(tan, R: int, dtype=torch.float32, reps: int = 3, cache_path: str | 
             cache = {}
     if key in cache and cands is None:
         best = cache[key]["setting"]
-        tan.tune(**best)
+        tan.tune(**{**DEFAULTS, **best})
         return dict(cache[key], cached=True)
     gen = torch.Generator("cuda").manual_seed(seed)
     p = torch.randn((tan.N, R), device="cuda", dtype=dtype, generator=gen)
@@ -109,11 +140,11 @@ def autotune(tan, R: int, dtype=torch.float32, reps: int = 3, cache_path: str | 
     results = []
     t0 = time.time()
     for c in (cands or candidates(R, dtype)):
-        tan.tune(**c)
+        tan.tune(**{**DEFAULTS, **c})
         results.append((time_setting(tan, p, y, reps), c))
     results.sort(key=lambda r: r[0])
     best_ms, best = results[0]
-    tan.tune(**best)
+    tan.tune(**{**DEFAULTS, **best})
     rec = {"setting": best, "ms": best_ms, "tried": [{"ms": ms, **c} for ms, c in results],
            "tune_s": time.time() - t0}
     if cache_path:

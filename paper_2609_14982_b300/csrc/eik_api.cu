@@ -287,6 +287,12 @@ int tangent_tune(eik_tangent *tt, const eik_opts *o)
     if (o->schedule < EIK_SCHED_PERSISTENT || o->schedule > EIK_SCHED_CLUSTER) { eik::set_error("bad schedule"); return EIK_ERR_INVALID; }
     if (o->rhs_chunk < 0 || o->ctas_per_sm < 0 || !(o->wait_timeout_s > 0) || o->block_lu_min < 0) { eik::set_error("bad tuning values"); return EIK_ERR_INVALID; }
     Tangent *t = tt->impl;
+    if (o->split_dirs) {
+        int rc = EIK_OK;
+        EIK_GUARD({ rc = eik::enable_split(t); });
+        if (rc) return rc;
+    }
+    t->opts.split_dirs = o->split_dirs ? 1 : 0;
     t->opts.schedule = o->schedule;
     t->opts.ctas_per_sm = o->ctas_per_sm;
     t->opts.rhs_chunk = o->rhs_chunk;

@@ -1541,22 +1541,38 @@ void launch_sample(long long N, int S, int n_rec, const int *rec, const double *
 }
 
 // ---------------------------------------------------------------- host side
-int ensure_workspace(Tangent *t, size_t vec_bytes, size_t blk_elems)
+int ensure_workspace(Tangent *t, size_t vec_bytes, size_t blk_elems, bool TR)
 {
-    if (vec_bytes > t->ws_vec_bytes) {
-        if (t->ws_vec) cudaFree(t->ws_vec);
-        t->ws_vec = nullptr;
-        t->ws_vec_bytes = 0;
-        EIK_CHECK(cudaMalloc(&t->ws_vec, vec_bytes));
-        t->ws_vec_bytes = vec_bytes;
+    const bool own = split_lane(t, TR);
+    void *&vec = own ? t->lane_t.ws_vec : t->ws_vec;
+    size_t &vec_n = own ? t->lane_t.ws_vec_bytes : t->ws_vec_bytes;
+    double *&blk = own ? t->lane_t.ws_blk : t->ws_blk;
+    size_t &blk_n = own ? t->lane_t.ws_blk_elems : t->ws_blk_elems;
+    if (vec_bytes > vec_n) {
+        if (vec) cudaFree(vec);
+        vec = nullptr;
+        vec_n = 0;
+        EIK_CHECK(cudaMalloc(&vec, vec_bytes));
+        vec_n = vec_bytes;
     }
-    if (blk_elems > t->ws_blk_elems) {
-        if (t->ws_blk) cudaFree(t->ws_blk);
-        t->ws_blk = nullptr;
-        t->ws_blk_elems = 0;
-        EIK_CHECK(cudaMalloc(&t->ws_blk, blk_elems * sizeof(double)));
-        t->ws_blk_elems = blk_elems;
+    if (blk_elems > blk_n) {
+        if (blk) cudaFree(blk);
+        blk = nullptr;
+        blk_n = 0;
+        EIK_CHECK(cudaMalloc(&blk, blk_elems * sizeof(double)));
+        blk_n = blk_elems;
     }
+    return EIK_OK;
+}
+
+int enable_split(Tangent *t)
+{
+    if (t->lane_t.ticket) return EIK_OK;
+    Lane &L = t->lane_t;
+    EIK_CHECK(cudaMalloc(&L.item_done, (size_t)std::max(t->nitems, 1) * sizeof(int) + 64));
+    EIK_CHECK(cudaMalloc(&L.done, (size_t)t->S * std::max(t->maxL, 1) * sizeof(int) + 64));
+    EIK_CHECK(cudaMalloc(&L.ticket, 4 * sizeof(int) + 64));
+    EIK_CHECK(cudaMemset(L.ticket, 0, 4 * sizeof(int)));
     return EIK_OK;
 }
 
@@ -1694,7 +1710,7 @@ static int launch_cluster(Tangent *t, const TravParams &P, cudaStream_t st)
     B.tab = t->maxL + 1;
     // keep the six slots and the level tables within 160 KB of shared memory
     while (B.tp > 32 && CL_SLOTS * cl_slot_bytes<T>(B.tp) + 3 * (size_t)B.tab * sizeof(int) > 160 * 1024) B.tp /= 2;
-    B.ticket = t->ticket + 1;
+    B.ticket = P.ticket + 1;
     if (W == 4) return launch_cluster_u<T, V, TR, 4>(t, B, t->S, st);
     if (W == 2) return launch_cluster_u<T, V, TR, 2>(t, B, t->S, st);
     return launch_cluster_u<T, V, TR, 1>(t, B, t->S, st);
@@ -1836,7 +1852,7 @@ static bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 int source_sum(Tangent *t, int w, void *g, long long ld_g, int dtype, cudaStream_t st, bool accumulate)
 {
     const int acc = accumulate ? 1 : 0;
-    const void *xp = t->ws_vec;
+    const void *xp = lane_ws(t, true);    // the reverse field of the last transpose traversal
     const int V = dtype == EIK_F32 ? 4 : 2;
     const int L = w / V;
     if (w % V == 0 && ld_g % V == 0 && aligned16(xp) && aligned16(g) && L <= 256) {
@@ -1886,12 +1902,15 @@ static TravParams make_params(Tangent *t, bool TR, int mode, const void *inp, in
     P.items = TR ? t->items_bwd : t->items_fwd;
     P.ebeg = TR ? t->ebeg_bwd : t->ebeg_fwd;
     P.item_cnt = t->item_cnt + (TR ? (size_t)t->S * t->maxL : 0);
-    P.done = t->done; P.ticket = t->ticket; P.err = t->err;
+    const bool own = split_lane(t, TR);
+    P.done = own ? t->lane_t.done : t->done;
+    P.ticket = own ? t->lane_t.ticket : t->ticket;
+    P.err = t->err;
     P.deps = TR ? t->deps_bwd : t->deps_fwd;
     // while a test hold is in place every item takes the level wait it targets
     P.ndeps = t->opts.item_deps && t->holds.empty() ? (TR ? t->ndeps_bwd : t->ndeps_fwd) : nullptr;
-    P.item_done = t->item_done;
-    P.blk_desc = t->blk_desc; P.blk_off = t->blk_off; P.binv = t->binv; P.ws = t->ws_blk;
+    P.item_done = own ? t->lane_t.item_done : t->item_done;
+    P.blk_desc = t->blk_desc; P.blk_off = t->blk_off; P.binv = t->binv; P.ws = own ? t->lane_t.ws_blk : t->ws_blk;
     P.lu = t->lu; P.piv = t->piv; P.blk_lu_min = t->opts.block_lu_min;
     P.timeout_ns = (unsigned long long)(t->opts.wait_timeout_s * 1e9);
     P.lvl = t->lvl_d; P.blk_lvl = t->blk_lvl_d; P.nlev = t->nlev_d; P.order = t->order_d;
@@ -1918,12 +1937,12 @@ int traverse(Tangent *t, bool TR, int mode, const void *in, int shared_in, int R
     }
     // the transported field always lives in the canonical-order workspace
     size_t need_vec = (size_t)t->S * t->N * Rc * esz;
-    int rc = ensure_workspace(t, need_vec, (size_t)t->ws_rows * Rc);
+    int rc = ensure_workspace(t, need_vec, (size_t)t->ws_rows * Rc, TR);
     if (rc) return rc;
     for (int r0 = 0; r0 < R; r0 += Rc) {
         const int w = std::min(Rc, R - r0);
         const char *inp = static_cast<const char *>(in) + r0 * esz;
-        char *xp = static_cast<char *>(t->ws_vec);
+        char *xp = static_cast<char *>(lane_ws(t, TR));
         char *outp = out_full ? static_cast<char *>(out_full) + r0 * esz : nullptr;
         char *auxp = out_aux ? static_cast<char *>(out_aux) + r0 * esz : nullptr;
         TravParams P = make_params(t, TR, mode, inp, shared_in, w, R, xp, outp, auxp, sum_sources, dtype);
@@ -1978,7 +1997,7 @@ static int launch_batch(Tangent *const *ts, int ntan, const TravParams *Ps, cons
     B.tp = std::min(512, (4 / W) * (threads / std::max(1, min_lanes / W)));
     B.tab = tab;
     while (B.tp > 32 && CL_SLOTS * cl_slot_bytes<T>(B.tp) + 3 * (size_t)B.tab * sizeof(int) > 160 * 1024) B.tp /= 2;
-    B.ticket = t0->ticket + 1;
+    B.ticket = Ps[0].ticket + 1;
     const int units = B.unit_ptr[ntan];
     if (W == 4) return launch_cluster_u<T, V, TR, 4>(t0, B, units, st);
     if (W == 2) return launch_cluster_u<T, V, TR, 2>(t0, B, units, st);
@@ -2003,11 +2022,11 @@ int traverse_batch(Tangent *const *ts, int ntan, bool TR, const void *const *in,
         if (t->device != ts[0]->device) { set_error("batch: tangents on different devices"); return EIK_ERR_INVALID; }
         while (R[k] % V) V >>= 1;
         // every right-hand side of every tangent in one pass: the workspace holds them all
-        int rc = ensure_workspace(t, (size_t)t->S * t->N * R[k] * esz, (size_t)t->ws_rows * R[k]);
+        int rc = ensure_workspace(t, (size_t)t->S * t->N * R[k] * esz, (size_t)t->ws_rows * R[k], TR);
         if (rc) return rc;
     }
     for (int k = 0; k < ntan; ++k)
-        Ps[k] = make_params(ts[k], TR, MODE_J, in[k], TR ? 0 : 1, R[k], R[k], ts[k]->ws_vec, nullptr,
+        Ps[k] = make_params(ts[k], TR, MODE_J, in[k], TR ? 0 : 1, R[k], R[k], lane_ws(ts[k], TR), nullptr,
                             TR ? nullptr : out[k], TR ? 1 : 0, dtype);
     int rc;
     if (dtype == EIK_F32) {

@@ -77,6 +77,20 @@ struct PointData {
     std::vector<double> corner_xyz;  // host [S][8][3] corner positions
 };
 
+// Per-direction launch state of the traversal: the transported field's workspace, the
+// block right-hand sides and the completion counters and ticket of the persistent and
+// cluster schedules.  The forward direction uses the Tangent's own fields; with
+// opts.split_dirs the transpose uses Tangent::lane_t, so the two may run concurrently.
+struct Lane {
+    void *ws_vec = nullptr;
+    size_t ws_vec_bytes = 0;
+    double *ws_blk = nullptr;
+    size_t ws_blk_elems = 0;
+    int *item_done = nullptr;     // [nitems]
+    int *done = nullptr;          // [S][maxL]
+    int *ticket = nullptr;        // [4]
+};
+
 struct Tangent {
     int S = 0;
     long long N = 0;
@@ -184,7 +198,16 @@ struct Tangent {
     std::map<std::vector<long long>, cudaGraphExec_t> sweep_graphs;
     // off-grid point sources (tangent_build_points); pts.K == 0 for node sources
     PointData pts;
+    // the transpose direction's own launch state (opts.split_dirs)
+    Lane lane_t;
 };
+
+// whether the transpose direction runs on its own launch state
+inline bool split_lane(const Tangent *t, bool TR) { return TR && t->opts.split_dirs && t->lane_t.ticket; }
+// the transported field's workspace of a direction
+inline void *lane_ws(const Tangent *t, bool TR) { return split_lane(t, TR) ? t->lane_t.ws_vec : t->ws_vec; }
+// allocate the transpose's counters and ticket (once)
+int enable_split(Tangent *t);
 
 // src_f (host [S][ndim] fractional logical coordinates) selects point sources; then
 // src_node is ignored
@@ -220,7 +243,7 @@ int traverse_batch(Tangent *const *ts, int ntan, bool TR, const void *const *in,
 int sweep(Tangent *t, bool transpose, const void *b, int R, void *x, int dtype,
           const eik_opts *opts, int *cycles, cudaStream_t stream);
 
-int ensure_workspace(Tangent *t, size_t vec_bytes, size_t blk_elems);
+int ensure_workspace(Tangent *t, size_t vec_bytes, size_t blk_elems, bool TR = false);
 // g (row stride ld_g) = sum over sources of c_a x_a for the w columns in the workspace, or
 // g += that sum when accumulate
 int source_sum(Tangent *t, int w, void *g, long long ld_g, int dtype, cudaStream_t st, bool accumulate = false);

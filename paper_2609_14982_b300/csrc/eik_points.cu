@@ -316,11 +316,11 @@ int seed_scatter(Tangent *t, int w, void *g, long long ld_g, bool per_source, co
     const unsigned blocks = (unsigned)((w + 63) / 64);
     if (dtype == EIK_F32)
         k_seed_scatter<float><<<blocks, 64, 0, st>>>(t->S, pd.K, t->N, w, pd.node, pd.phim, pd.r, t->pos,
-                                                    (const float *)t->ws_vec, n_y, rho, (const float *)y, ld_y,
+                                                    (const float *)lane_ws(t, true), n_y, rho, (const float *)y, ld_y,
                                                     (float *)g, ld_g, per_source ? 1 : 0);
     else
         k_seed_scatter<double><<<blocks, 64, 0, st>>>(t->S, pd.K, t->N, w, pd.node, pd.phim, pd.r, t->pos,
-                                                     (const double *)t->ws_vec, n_y, rho, (const double *)y, ld_y,
+                                                     (const double *)lane_ws(t, true), n_y, rho, (const double *)y, ld_y,
                                                      (double *)g, ld_g, per_source ? 1 : 0);
     EIK_CHECK_LAUNCH();
     return EIK_OK;

@@ -919,6 +919,8 @@ void free_tangent(Tangent *t)
                     t->ws_in, t->lvl_d, t->blk_lvl_d, t->nlev_d, t->order_d};
     for (void *p : ptrs) if (p) cudaFree(p);
     free_point_data(t->pts);
+    void *lane[] = {t->lane_t.ws_vec, t->lane_t.ws_blk, t->lane_t.item_done, t->lane_t.done, t->lane_t.ticket};
+    for (void *p : lane) if (p) cudaFree(p);
     if (t->params_d) cudaFree((void *)t->params_d);
     for (void *p : t->sweep_w) if (p) cudaFree(p);
     if (t->sweep_flags) cudaFree(t->sweep_flags);
@@ -1496,6 +1498,10 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
     TRY(cudaGetLastError());
     TRY(cudaStreamSynchronize(st));
 #undef TRY
+    if (opts->split_dirs) {
+        int rc = enable_split(t);
+        if (rc) return fail(rc);
+    }
     if (src_f) {
         // point sources: model factors at the corners and z = A^-1 e (a traversal of the
         // finished tangent)
