@@ -347,6 +347,9 @@ def run_ours(args):
                 "peak_kind": f"{peak_kind} hbm_gbs",
                 "concurrent_with_other_direction": concurrent,
                 "pair_achieved_gbs": round((ab["fwd"] + ab["bwd"]) / (ms / 1e3) / 1e9, 1),
+                "pair_frac": round((ab["fwd"] + ab["bwd"]) / (ms / 1e3) / 1e9 / peak, 4),
+                "pair_note": "J p and J^T y algorithmic bytes over the whole step; with the directions concurrent "
+                             "each kernel's own duration covers the time it shares the GPU",
                 "other_direction": {"dir": other, "ms": round(mb, 4), "includes": "k_source_sum_vec",
                                     "frac": round(ab[other] / (mb / 1e3) / 1e9 / peak, 4)}}
 
