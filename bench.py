@@ -288,12 +288,34 @@ def run_ours(args):
     y_d = torch.empty_like(y)
 
     def e2e_step():
-        p_d.copy_(p_h, non_blocking=True)
-        y_d.copy_(y_h, non_blocking=True)
-        pair(p_d, y_d)
-        reduce_model_gradient(gvec)
-        drec_h.copy_(d_rec, non_blocking=True)
-        g_h.copy_(gvec, non_blocking=True)
+        if not concurrent:
+            p_d.copy_(p_h, non_blocking=True)
+            y_d.copy_(y_h, non_blocking=True)
+            pair(p_d, y_d)
+            reduce_model_gradient(gvec)
+            drec_h.copy_(d_rec, non_blocking=True)
+            g_h.copy_(gvec, non_blocking=True)
+            return
+        # each direction on its own stream: its input copy, its traversal, its result copy,
+        # so the copy of one direction overlaps the other's traversal
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        sa, sb = pair_streams
+        sa.wait_event(fork)
+        sb.wait_event(fork)
+        with torch.cuda.stream(sb):
+            y_d.copy_(y_h, non_blocking=True)
+            tan.apply_T(y_d, sum_sources=True, g=gvec)
+            reduce_model_gradient(gvec)
+            g_h.copy_(gvec, non_blocking=True)
+        with torch.cuda.stream(sa):
+            p_d.copy_(p_h, non_blocking=True)
+            tan.apply(p_d, shared_model=True, d_rec=d_rec)
+            drec_h.copy_(d_rec, non_blocking=True)
+        for st_ in pair_streams:
+            join = torch.cuda.Event()
+            join.record(st_)
+            stream.wait_event(join)
 
     for _ in range(max(1, args.warmup)):
         e2e_step()
