@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "J·v+Jᵀ·w node-updates/s per B300 vs GPU sweeping; % HBM roofline"
 UNIT = "node-updates/s"
 WORKLOAD = "3d-101x101x51-S25-R64 (config: 3-D tomography-scale apply)"
+KRYLOV_CHUNK = 256      # item size of the tangents of the one-right-hand-side Krylov workloads
 
 
 def _peaks():
@@ -463,7 +464,8 @@ def run_lsqr(args):
     torch.cuda.synchronize()
     t_state = time.time() - t0
     t0 = time.time()
-    tan = eik.Tangent(dg, T, s, src, rec=wl.rec)
+    # one right-hand side per Krylov step: 256-position items (one pass of 256 threads)
+    tan = eik.Tangent(dg, T, s, src, rec=wl.rec, opts=eik.default_opts(chunk=KRYLOV_CHUNK))
     torch.cuda.synchronize()
     t_setup = time.time() - t0
     del T
@@ -521,7 +523,7 @@ def run_gn(args):
     torch.cuda.synchronize()
     t_state = time.time() - t0
     t0 = time.time()
-    tan = eik.Tangent(dg, T, s, src, rec=wl.rec, opts=eik.default_opts(model=eik.MODEL_VELOCITY))
+    tan = eik.Tangent(dg, T, s, src, rec=wl.rec, opts=eik.default_opts(model=eik.MODEL_VELOCITY, chunk=KRYLOV_CHUNK))
     torch.cuda.synchronize()
     t_setup = time.time() - t0
     rec = torch.as_tensor(np.asarray(wl.rec, dtype=np.int64), device="cuda")
@@ -719,7 +721,7 @@ def gauss_newton_iteration_config4(lsqr_iters: int = 20) -> dict:
     T, cyc = eik.eik_forward(dg, s, wl.src, opts=eik.default_opts(eik_fp32=1))
     torch.cuda.synchronize()
     t1 = time.time()
-    tan = eik.Tangent(dg, T, s, wl.src, rec=wl.rec)
+    tan = eik.Tangent(dg, T, s, wl.src, rec=wl.rec, opts=eik.default_opts(chunk=KRYLOV_CHUNK))
     torch.cuda.synchronize()
     t2 = time.time()
     del T

@@ -78,7 +78,9 @@ typedef struct {
     double lu_pivot_tol;       /* |pivot| below this marks a block singular (default 1e-13) */
     int schedule;              /* eik_schedule (default persistent) */
     int threads;               /* CTA size of the traversal kernels (default 256) */
-    int chunk;                 /* singleton nodes per work item (default 0 = auto) */
+    int chunk;                 /* singleton nodes per work item (default 0 = 64; at most 256:
+                                  items above 64 suit few right-hand sides, e.g. R = 1 in
+                                  Krylov loops, and run in the persistent or cluster schedule) */
     int ctas_per_sm;           /* persistent grid = SMs x this (default 0 = occupancy) */
     double wait_timeout_s;     /* bound on any device-side wait (default 2 s) */
     /* eik_forward */

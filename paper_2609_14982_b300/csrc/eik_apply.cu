@@ -564,13 +564,13 @@ template <typename T> __device__ __forceinline__ void cp_async_t(T *dst, const T
     else cp_async4(dst, src);
 }
 
-template <typename T> struct ItemStage {
-    T cq[ITEM_MAX];
-    T ew[MAX_ROW * ITEM_MAX];
-    int perm[ITEM_MAX];
-    int rec[ITEM_MAX];
-    int rp[ITEM_MAX + 1];        // raw local edge offsets (subtract ebx)
-    int en[MAX_ROW * ITEM_MAX];
+template <typename T, int IM = ITEM_MAX> struct ItemStage {
+    T cq[IM];
+    T ew[MAX_ROW * IM];
+    int perm[IM];
+    int rec[IM];
+    int rp[IM + 1];              // raw local edge offsets (subtract ebx)
+    int en[MAX_ROW * IM];
     int deps[DEP_MAX];           // items holding the upstream rows (persistent schedule)
     int nd;                      // their number; -1: wait for the whole previous level
     int4 it;                     // item descriptor
@@ -588,8 +588,8 @@ __device__ __forceinline__ const T *input_row(const TravParams &P, long long a, 
     return in + (a * P.N + v) * P.ld_in;
 }
 
-template <typename T, int V, bool TR>
-__device__ __forceinline__ void run_stage_singletons(const TravParams &P, const ItemStage<T> &S, const unsigned char *tile,
+template <typename T, int V, bool TR, int IM>
+__device__ __forceinline__ void run_stage_singletons(const TravParams &P, const ItemStage<T, IM> &S, const unsigned char *tile,
                                                 int G)
 {
     const int lane = threadIdx.x % G, slot = threadIdx.x / G, nslot = blockDim.x / G;
@@ -641,8 +641,8 @@ __device__ __forceinline__ void run_stage_singletons(const TravParams &P, const 
 // g + (W-1) G of positions k0 + q * nslot, q < U, decodes each row once for its W lanes
 // and issues all its upstream loads before any sum.  Same arithmetic, in the same order,
 // as run_stage_singletons.
-template <typename T, int V, int W, int U, bool TR>
-__device__ __forceinline__ void run_stage_lanes(const TravParams &P, const ItemStage<T> &S, const unsigned char *tile,
+template <typename T, int V, int W, int U, bool TR, int IM>
+__device__ __forceinline__ void run_stage_lanes(const TravParams &P, const ItemStage<T, IM> &S, const unsigned char *tile,
                                                 int lanes)
 {
     const int G = lanes / W;
@@ -743,8 +743,8 @@ __device__ __forceinline__ void st_relaxed(int *p, int v)
 }
 
 // structure of item S.idx (descriptor already in S) into S, by all threads of the CTA
-template <typename T>
-__device__ __forceinline__ void issue_structure(const TravParams &P, ItemStage<T> &S)
+template <typename T, int IM>
+__device__ __forceinline__ void issue_structure(const TravParams &P, ItemStage<T, IM> &S)
 {
     const int i = S.idx;
     const int4 it = S.it;
@@ -776,8 +776,8 @@ __device__ __forceinline__ void issue_structure(const TravParams &P, ItemStage<T
 }
 
 // input rows of item S (structure visible) into the tile, 16 bytes per copy
-template <typename T, bool TR>
-__device__ __forceinline__ void issue_input(const TravParams &P, const ItemStage<T> &S, unsigned char *tile)
+template <typename T, bool TR, int IM>
+__device__ __forceinline__ void issue_input(const TravParams &P, const ItemStage<T, IM> &S, unsigned char *tile)
 {
     if (S.it.z < 0) return;
     const long long a = S.it.x;
@@ -794,8 +794,8 @@ __device__ __forceinline__ void issue_input(const TravParams &P, const ItemStage
 }
 
 // descriptor of ticket i into S (one thread)
-template <typename T>
-__device__ __forceinline__ void load_desc(const TravParams &P, ItemStage<T> &S, int i)
+template <typename T, int IM>
+__device__ __forceinline__ void load_desc(const TravParams &P, ItemStage<T, IM> &S, int i)
 {
     S.idx = i;
     if (i < P.nitems) {
@@ -807,11 +807,11 @@ __device__ __forceinline__ void load_desc(const TravParams &P, ItemStage<T> &S, 
     S.nd = -1;
 }
 
-template <typename T, int V, bool TR, int W = 0, int U = 1>
+template <typename T, int V, bool TR, int W = 0, int U = 1, int IM = ITEM_MAX>
 __global__ void __launch_bounds__(256, (W * U >= 4) ? 2 : 4) k_traverse_persistent(TravParams P, int G, int tile_bytes)
 {
     extern __shared__ __align__(128) unsigned char dyn[];
-    __shared__ ItemStage<T> stg[2];
+    __shared__ ItemStage<T, IM> stg[2];
     __shared__ int s_ok;
     const int tid = threadIdx.x;
     const int nitems = P.nitems;
@@ -830,8 +830,8 @@ __global__ void __launch_bounds__(256, (W * U >= 4) ? 2 : 4) k_traverse_persiste
     if (tile_bytes) issue_input<T, TR>(P, stg[0], dyn);
     cp_async_commit();
     for (int b = 0;; b ^= 1) {
-        ItemStage<T> &C = stg[b];
-        ItemStage<T> &Nx = stg[b ^ 1];
+        ItemStage<T, IM> &C = stg[b];
+        ItemStage<T, IM> &Nx = stg[b ^ 1];
         const int4 it = C.it;
         const int i = C.idx;
         // ---- wait (warp 0) for the items holding the upstream rows
@@ -1720,6 +1720,11 @@ template <typename T, int V, bool TR>
 static int launch_traverse(Tangent *t, TravParams &P, int G, cudaStream_t st)
 {
     if (t->opts.schedule == EIK_SCHED_CLUSTER) return launch_cluster<T, V, TR>(t, P, st);
+    if (t->item_max > ITEM_MAX && t->opts.schedule != EIK_SCHED_PERSISTENT) {
+        set_error("items of %d positions run in the persistent or cluster schedule only (build with chunk <= %d)",
+                  t->item_max, ITEM_MAX);
+        return EIK_ERR_INVALID;
+    }
     const size_t rowb = (size_t)P.R * sizeof(T);
     const bool staged_ok = rowb % 16 == 0 && rowb >= 64 && (P.ld_in * sizeof(T)) % 16 == 0 &&
                            (P.ld_x * sizeof(T)) % 16 == 0 && V * sizeof(T) == 16;
@@ -1804,7 +1809,8 @@ static int launch_traverse(Tangent *t, TravParams &P, int G, cudaStream_t st)
     const int lanes = P.R / V;
     const int want = t->opts.pass_units > 0 ? t->opts.pass_units : 1;
     void (*kern)(TravParams, int, int) = k_traverse_persistent<T, V, TR>;
-    if (want >= 4 && lanes % 4 == 0 && lanes / 4 <= threads) kern = k_traverse_persistent<T, V, TR, 4, 1>;
+    if (t->item_max > ITEM_MAX) kern = k_traverse_persistent<T, V, TR, 0, 1, ITEM_CAP>;   // large items (R small)
+    else if (want >= 4 && lanes % 4 == 0 && lanes / 4 <= threads) kern = k_traverse_persistent<T, V, TR, 4, 1>;
     else if (want >= 2 && lanes % 2 == 0 && lanes / 2 <= threads) kern = k_traverse_persistent<T, V, TR, 2, 1>;
     EIK_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = t->opts.ctas_per_sm;

@@ -27,6 +27,9 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
 // Capacity of one work item (positions staged in shared memory); the build option
 // eik_opts.chunk picks the item size actually used (default: the capacity).
 constexpr int ITEM_MAX = 64;
+// Largest item a tangent may be built with (eik_opts.chunk); items above ITEM_MAX run only
+// in the persistent schedule (a kernel instance with this capacity), e.g. for R = 1.
+constexpr int ITEM_CAP = 256;
 
 // Most dependencies recorded per work item.
 constexpr int DEP_MAX = 32;

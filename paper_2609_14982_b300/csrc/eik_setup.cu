@@ -1362,7 +1362,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
 
     // ---- traversal work items: level-major over sources
     {
-        int chunk = opts->chunk > 0 ? std::min(opts->chunk, ITEM_MAX) : ITEM_MAX;
+        int chunk = opts->chunk > 0 ? std::min(opts->chunk, ITEM_CAP) : ITEM_MAX;
         t->item_max = chunk;
         std::vector<std::vector<int4>> per((size_t)S * maxL);
         std::vector<int> blk_ptr(S + 1, 0);
