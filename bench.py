@@ -776,13 +776,27 @@ def run_state(args):
     from paper_2609_14982_b300 import workloads as W
     torch.cuda.set_device(0)
     rows = []
-    for wl, fp32 in ((W.config3(), 0), (W.config3(), 1), (W.config4(), 1)):
+    runs = ((W.config3(), 0), (W.config3(), 1), (W.config4(), 1))
+    if args.state_cycles > 0:
+        runs = runs[1:2]     # a short profiling case: the 3-D apply grid, FP32 far field, a few cycles
+    for wl, fp32 in runs:
         g = wl.grid
         dg = eik.DeviceGrid(g)
         s = torch.tensor(wl.s, device="cuda")
-        eik.eik_forward(dg, s, wl.src[:1], opts=eik.default_opts(eik_fp32=fp32))   # warm-up (module load)
+        if args.state_cycles <= 0:
+            eik.eik_forward(dg, s, wl.src[:1], opts=eik.default_opts(eik_fp32=fp32))   # warm-up (module load)
         torch.cuda.synchronize()
         t0 = time.time()
+        if args.state_cycles > 0:
+            try:
+                eik.eik_forward(dg, s, wl.src, opts=eik.default_opts(eik_fp32=fp32, eik_max_cycles=args.state_cycles))
+            except eik.EikError as e:
+                if e.code != -4:      # EIK_ERR_NOT_CONVERGED is expected after so few cycles
+                    raise
+            torch.cuda.synchronize()
+            rows.append({"grid": list(g.n), "sources": wl.S, "cycles": args.state_cycles,
+                         "seconds": round(time.time() - t0, 3)})
+            continue
         T, cyc = eik.eik_forward(dg, s, wl.src, opts=eik.default_opts(eik_fp32=fp32))
         torch.cuda.synchronize()
         sec = time.time() - t0
@@ -791,6 +805,9 @@ def run_state(args):
         rows.append({"grid": list(g.n), "sources": wl.S, "fp32_far_field": bool(fp32), "seconds": round(sec, 3),
                      "cycles": cyc, "node_updates_per_s": upd / sec})
         del T
+    if args.state_cycles > 0:
+        print(json.dumps({"workload": "state solve, profiling case", "runs": rows}), flush=True)
+        return
     out = {"metric": "eik_forward node-updates/s (LF sweeping, all sources)", "value": rows[-1]["node_updates_per_s"],
            "unit": "node-updates/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": rows[-1]["seconds"] * 1e3,
            "higher_is_better": True, "dtype": "f64 (f32 far field where marked)", "data": "synthetic",
@@ -938,6 +955,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--schedule", choices=["persistent", "levels", "staged", "cluster"], default="persistent")
+    ap.add_argument("--state-cycles", type=int, default=0,
+                    help="--workload state: only the 3-D apply grid (FP32 far field) for this many cycles (profiling)")
     ap.add_argument("--split-dirs", action="store_true",
                     help="run J p and J^T y of a step at once on two streams (2 CTAs per SM each unless given)")
     ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
