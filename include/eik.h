@@ -193,6 +193,19 @@ int eik_forward_noalloc(const eik_grid *g, const double *s, int S, const int *sr
                         double *T, const eik_opts *opts, int *cycles, eik_stream stream);
 
 /*
+ * eik_forward_warm -- eik_forward started from a given traveltime field instead of the
+ * homogeneous solution (tau = T_init / T0 at every non-fixed node; tau = 1 where T_init is
+ * not positive and finite): the re-setup of an outer Gauss-Newton iteration (Alg. 1 Phase
+ * I after a model update) starts from the previous iteration's state.  The sweeps, the
+ * stopping rule and the result's fixed point are those of eik_forward; the state agrees
+ * with a cold start to the stopping tolerance, in fewer cycles when T_init is close.
+ *   T_init   device [S][N] (may be the same buffer as T)
+ *   other arguments and errors as eik_forward
+ */
+int eik_forward_warm(const eik_grid *g, const double *s, int S, const int *src_node,
+                     const double *T_init, double *T, const eik_opts *opts, int *cycles, eik_stream stream);
+
+/*
  * eik_forward_points -- the state solve of eik_forward for point sources between grid
  * nodes (the off-grid sources of Sec. 3.1 / 4.4; the paper gives the source treatment no
  * formula).  Reading: source a sits at fractional logical coordinates f[a] (0 <= f_d <=

@@ -101,6 +101,18 @@ __global__ void k_point_radius(int S, const double *__restrict__ r, const double
     t0_fp64[a] = ss[a] * dist64;
 }
 
+// warm start: tau = T_init / T0 at every node that is not fixed (T_init [S][N], source-major)
+__global__ void k_tau_from_T(long long N, int S, const double *__restrict__ T_init, const double *__restrict__ T0,
+                             const unsigned char *__restrict__ fixed, double *__restrict__ tau)
+{
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= N * S) return;
+    const long long i = v / S, a = v - i * S;
+    if (fixed[v] || !(T0[v] > 0.0)) return;
+    const double t = T_init[a * N + i] / T0[v];
+    if (t > 0.0 && t < 1e30) tau[v] = t;     // keep tau = 1 where the given value is unusable
+}
+
 struct LFParams {
     GridDesc g;
     int S, order, h, lo0, hi0;
@@ -379,7 +391,8 @@ using namespace eik;
 // node sources (src_node) or point sources (src_f: host [S][ndim] fractional logical
 // coordinates)
 static int forward_impl(const eik_grid *gin, const double *s, int S, const int *src_node, const double *src_f,
-                        double *T, const eik_opts *opts_in, int *cycles, eik_stream stream)
+                        double *T, const eik_opts *opts_in, int *cycles, eik_stream stream,
+                        const double *T_init = nullptr)
 {
     try {
         if (!gin || (gin->ndim != 2 && gin->ndim != 3) || !gin->xyz || !s || !T || (!src_node && !src_f) || S <= 0) {
@@ -441,6 +454,10 @@ static int forward_impl(const eik_grid *gin, const double *s, int S, const int *
             k_t0_threshold<<<(S + 127) / 128, 128, 0, st>>>(S, s, src_d, opts->eik_fp64_radius * hmax, t0_fp64);
         }
         TRY(cudaGetLastError());
+        if (T_init) {
+            k_tau_from_T<<<(unsigned)((SN + 255) / 256), 256, 0, st>>>(N, S, T_init, T0, fixed, tau);
+            TRY(cudaGetLastError());
+        }
         LFParams P{};
         P.g = g; P.S = S; P.G = G; P.s = s; P.T0 = T0; P.g0 = g0; P.alpha = alpha; P.fixed = fixed; P.tau = tau;
         P.dmax = dmax; P.active = active;
@@ -471,6 +488,13 @@ extern "C" int eik_forward(const eik_grid *gin, const double *s, int S, const in
 {
     if (!src_node) { set_error("bad eik_forward arguments"); return EIK_ERR_INVALID; }
     return forward_impl(gin, s, S, src_node, nullptr, T, opts_in, cycles, stream);
+}
+
+extern "C" int eik_forward_warm(const eik_grid *gin, const double *s, int S, const int *src_node,
+                                const double *T_init, double *T, const eik_opts *opts_in, int *cycles, eik_stream stream)
+{
+    if (!src_node || !T_init) { set_error("bad eik_forward_warm arguments"); return EIK_ERR_INVALID; }
+    return forward_impl(gin, s, S, src_node, nullptr, T, opts_in, cycles, stream, T_init);
 }
 
 extern "C" int eik_forward_points(const eik_grid *gin, const double *s, int S, const double *src_f, double *T,

@@ -29,7 +29,8 @@ EXPORTED = ["eik_opts_default", "eik_last_error", "eik_version", "eik_forward", 
             "gn_create", "gn_dims", "gn_apply", "gn_apply_T", "gn_lsmr_start", "gn_lsmr_iterate",
             "gn_lsmr_solution", "gn_free", "model_cells_to_nodes", "model_nodes_to_cells",
             "tangent_set_receivers", "tangent_apply_interp", "tangent_apply_interp_T", "gn_create_cells", "gn_rhs",
-            "tangent_apply_batch", "tangent_apply_T_batch", "eik_forward_points", "tangent_build_points"]
+            "tangent_apply_batch", "tangent_apply_T_batch", "eik_forward_points", "tangent_build_points",
+            "eik_forward_warm"]
 
 
 class EikError(RuntimeError):
@@ -80,6 +81,7 @@ def lib():
         L.tangent_build.argtypes = [C.POINTER(Grid_), P, P, I, P, P, I, C.POINTER(Opts), C.POINTER(P), P]
         L.tangent_build_points.argtypes = [C.POINTER(Grid_), P, P, I, P, P, I, C.POINTER(Opts), C.POINTER(P), P]
         L.eik_forward_points.argtypes = [C.POINTER(Grid_), P, I, P, P, C.POINTER(Opts), C.POINTER(I), P]
+        L.eik_forward_warm.argtypes = [C.POINTER(Grid_), P, I, P, P, P, C.POINTER(Opts), C.POINTER(I), P]
         L.tangent_apply.argtypes = [P, P, I, I, P, P, I, P]
         L.tangent_apply_T.argtypes = [P, P, I, I, P, P, I, P]
         L.tangent_solve.argtypes = [P, P, I, P, I, P]
@@ -215,14 +217,22 @@ def _check_state_args(dgrid: DeviceGrid, s: torch.Tensor, S: int, out: torch.Ten
                 raise ValueError(f"{name} is on {t.device}, the current device is cuda:{cur}")
 
 
-def eik_forward(dgrid: DeviceGrid, s: torch.Tensor, src, opts: Opts | None = None, out: torch.Tensor | None = None):
-    """First-arrival traveltimes [S, N] (float64) for the given source nodes."""
+def eik_forward(dgrid: DeviceGrid, s: torch.Tensor, src, opts: Opts | None = None, out: torch.Tensor | None = None,
+                T_init: torch.Tensor | None = None):
+    """First-arrival traveltimes [S, N] (float64) for the given source nodes; with T_init
+    [S, N] the sweeps start from that field (eik_forward_warm)."""
     src = torch.as_tensor(src, dtype=torch.int32).contiguous().cpu()
     S = int(src.numel())
     _check_state_args(dgrid, s, S, out)
     if out is None:
         out = torch.empty((S, dgrid.N), dtype=torch.float64, device=s.device)
     cyc = C.c_int(0)
+    if T_init is not None:
+        _check_state_args(dgrid, s, S, T_init)
+        _check(lib().eik_forward_warm(C.byref(dgrid.c), _dev(s, torch.float64, "s"), S, C.c_void_p(src.data_ptr()),
+                                      _dev(T_init, torch.float64, "T_init"), _dev(out, torch.float64, "T"),
+                                      C.byref(opts) if opts else None, C.byref(cyc), _stream()))
+        return out, cyc.value
     _check(lib().eik_forward(C.byref(dgrid.c), _dev(s, torch.float64, "s"), S, C.c_void_p(src.data_ptr()),
                              _dev(out, torch.float64, "T"), C.byref(opts) if opts else None, C.byref(cyc), _stream()))
     return out, cyc.value
