@@ -23,11 +23,30 @@ def tangent_bytes(S: int, N: int) -> int:
     return int(S) * int(N) * BYTES_PER_SOURCE_NODE
 
 
+class StateCache:
+    """The traveltimes of the last forward pass, so that the next state solve of the same
+    sources starts from them (eik_forward_warm): in an inversion loop the state of outer
+    iteration k+1 is solved from that of iteration k.  `cycles` records the sweep cycles
+    each forward pass used."""
+
+    def __init__(self):
+        self.T = None
+        self.key = None
+        self.cycles = []
+
+
 class SlownessToTraveltime(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, s, dgrid, src, rec, opts, budget_bytes):
+    def forward(ctx, s, dgrid, src, rec, opts, budget_bytes, cache=None):
         src = [int(a) for a in src]
-        T, _ = eik.eik_forward(dgrid, s, src, opts)
+        key = (id(dgrid), tuple(src))
+        if cache is not None and cache.T is not None and cache.key == key:
+            T, cyc = eik.eik_forward(dgrid, s, src, opts, T_init=cache.T)
+        else:
+            T, cyc = eik.eik_forward(dgrid, s, src, opts)
+        if cache is not None:
+            cache.T, cache.key = T.detach().clone(), key
+            cache.cycles.append(cyc)
         keep = tangent_bytes(len(src), dgrid.N) <= budget_bytes
         if keep:
             tan = eik.Tangent(dgrid, T, s, src, rec=rec, opts=opts)
@@ -56,7 +75,7 @@ class SlownessToTraveltime(torch.autograd.Function):
             g, _ = ctx.tan.apply_T(y, sum_sources=True)
             ctx.tan.free()
             ctx.tan = None
-            return g[:, 0], None, None, None, None, None
+            return g[:, 0], None, None, None, None, None, None
         # recompute the frozen state chunk by chunk; each chunk's source sum is added to
         # the gradient by the library (tangent_apply_T with sum_sources = 2)
         total = torch.zeros((ctx.dgrid.N, 1), dtype=torch.float64, device=s.device)
@@ -66,13 +85,15 @@ class SlownessToTraveltime(torch.autograd.Function):
             tan = eik.Tangent(ctx.dgrid, T, s, part, rec=ctx.rec, opts=ctx.opts)
             tan.apply_T(y[c0:c0 + ctx.chunk].contiguous(), sum_sources=True, g=total, accumulate=True)
             tan.free()
-        return total[:, 0], None, None, None, None, None
+        return total[:, 0], None, None, None, None, None, None
 
 
-def slowness_to_traveltime(s: torch.Tensor, dgrid, src, rec, opts=None, budget_bytes: int | None = None):
+def slowness_to_traveltime(s: torch.Tensor, dgrid, src, rec, opts=None, budget_bytes: int | None = None,
+                           cache: StateCache | None = None):
     """Receiver traveltimes [S, n_rec] of slowness s [N] (FP64, on the device).
-    budget_bytes bounds the memory kept for backward (default: half the free memory)."""
+    budget_bytes bounds the memory kept for backward (default: half the free memory);
+    with a StateCache the state solve starts from the previous call's traveltimes."""
     if budget_bytes is None:
         free, _ = torch.cuda.mem_get_info()
         budget_bytes = free // 2
-    return SlownessToTraveltime.apply(s, dgrid, src, rec, opts or eik.default_opts(), int(budget_bytes))
+    return SlownessToTraveltime.apply(s, dgrid, src, rec, opts or eik.default_opts(), int(budget_bytes), cache)

@@ -117,6 +117,31 @@ def test_autograd_recompute_policy_matches_cached():
     assert torch.allclose(gs[0], gs[1], rtol=0, atol=1e-13 * float(gs[0].abs().max()))
 
 
+def test_autograd_state_cache_warm_starts():
+    """With a StateCache the second forward pass (after a small model change) starts from
+    the first pass's traveltimes: fewer sweep cycles, and the same data and gradient as a
+    cold pass to the stopping tolerance."""
+    from paper_2609_14982_b300.autograd import StateCache
+    wl = W.config1()
+    g = wl.grid
+    srcs = [int(wl.src[0]), g.index(30, 0)]
+    dg = eik.DeviceGrid(g)
+    grad = torch.tensor(np.random.default_rng(4).standard_normal((2, len(wl.rec))), device=DEV)
+    cache = StateCache()
+    s0 = torch.tensor(wl.s, device=DEV)
+    slowness_to_traveltime(s0, dg, srcs, wl.rec, cache=cache)
+    s1 = (s0 * (1.0 + 0.01 * torch.sin(torch.tensor(g.xyz[:, 0], device=DEV)))).requires_grad_(True)
+    d_warm = slowness_to_traveltime(s1, dg, srcs, wl.rec, cache=cache)
+    (d_warm * grad).sum().backward()
+    g_warm = s1.grad.clone()
+    s1.grad = None
+    d_cold = slowness_to_traveltime(s1, dg, srcs, wl.rec)
+    (d_cold * grad).sum().backward()
+    assert cache.cycles[1] < cache.cycles[0]
+    assert float((d_warm - d_cold).detach().abs().max()) <= 1e-9 * float(d_cold.detach().abs().max())
+    assert float((g_warm - s1.grad).abs().max()) <= 1e-6 * float(s1.grad.abs().max())
+
+
 def _fd_mismatch(m):
     """Normwise mismatch between central differences of forward (h = 1e-4 relative) and
     the autograd gradient over 8 smooth directions, on the config-1 recipe refined m x."""
