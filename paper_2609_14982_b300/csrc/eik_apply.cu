@@ -1857,6 +1857,7 @@ static bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 // workspace holds (the reverse field of the last traversal, canonical order)
 int source_sum(Tangent *t, int w, void *g, long long ld_g, int dtype, cudaStream_t st, bool accumulate)
 {
+    NvtxRange range("source sum");
     const int acc = accumulate ? 1 : 0;
     const void *xp = lane_ws(t, true);    // the reverse field of the last transpose traversal
     const int V = dtype == EIK_F32 ? 4 : 2;
@@ -1926,6 +1927,7 @@ static TravParams make_params(Tangent *t, bool TR, int mode, const void *inp, in
 int traverse(Tangent *t, bool TR, int mode, const void *in, int shared_in, int R, void *out_full, void *out_aux,
              int sum_sources, int dtype, cudaStream_t st)
 {
+    NvtxRange range(TR ? (mode == MODE_J ? "J^T traversal" : "A^-T solve") : (mode == MODE_J ? "J traversal" : "A^-1 solve"));
     if (R <= 0) { set_error("R must be positive"); return EIK_ERR_INVALID; }
     if (!in) { set_error("input pointer is NULL"); return EIK_ERR_INVALID; }
     if (dtype != EIK_F32 && dtype != EIK_F64) { set_error("bad dtype"); return EIK_ERR_INVALID; }
@@ -2013,6 +2015,7 @@ static int launch_batch(Tangent *const *ts, int ntan, const TravParams *Ps, cons
 int traverse_batch(Tangent *const *ts, int ntan, bool TR, const void *const *in, const int *R, void *const *out,
                    int dtype, cudaStream_t st)
 {
+    NvtxRange range(TR ? "J^T batch" : "J batch");
     for (int k = 0; k < ntan; ++k)
         if (ts[k] && ts[k]->pts.K > 0) { set_error("batched applies take tangents of node sources only"); return EIK_ERR_INVALID; }
     if (ntan < 1 || ntan > CL_MAXTAN) { set_error("batch: 1..%d tangents", CL_MAXTAN); return EIK_ERR_INVALID; }

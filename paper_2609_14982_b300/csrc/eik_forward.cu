@@ -394,6 +394,7 @@ static int forward_impl(const eik_grid *gin, const double *s, int S, const int *
                         double *T, const eik_opts *opts_in, int *cycles, eik_stream stream,
                         const double *T_init = nullptr)
 {
+    NvtxRange range(src_f ? "eik_forward_points" : (T_init ? "eik_forward_warm" : "eik_forward"));
     try {
         if (!gin || (gin->ndim != 2 && gin->ndim != 3) || !gin->xyz || !s || !T || (!src_node && !src_f) || S <= 0) {
             set_error("bad eik_forward arguments");

@@ -540,6 +540,7 @@ int gn_lsmr_start(eik_gn *G, const void *b, eik_stream stream)
 
 int gn_lsmr_iterate(eik_gn *G, int iters, int use_graph, eik_stream stream)
 {
+    eik::NvtxRange range("LSMR iterations");
     if (!G || iters < 0) { set_error("bad gn_lsmr_iterate arguments"); return EIK_ERR_INVALID; }
     cudaStream_t st = (cudaStream_t)stream;
     if (use_graph && !G->exec) {

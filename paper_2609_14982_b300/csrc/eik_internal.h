@@ -10,6 +10,8 @@
 
 #include "eik.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace eik {
 
 struct TravParams;
@@ -23,6 +25,28 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
     } while (0)
 
 #define EIK_CHECK_LAUNCH() EIK_CHECK(cudaGetLastError())
+
+// NVTX range over a host scope (the phases of a call), for profilers that filter or
+// group kernels by range (ncu --nvtx); costs nothing when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
+// consecutive NVTX ranges over the phases of one host function: next() closes the open
+// phase and opens the named one; the last closes at scope exit
+struct NvtxPhase {
+    bool open = false;
+    void next(const char *name)
+    {
+        if (open) nvtxRangePop();
+        nvtxRangePushA(name);
+        open = true;
+    }
+    ~NvtxPhase() { if (open) nvtxRangePop(); }
+};
 
 // Capacity of one work item (positions staged in shared memory); the build option
 // eik_opts.chunk picks the item size actually used (default: the capacity).

@@ -170,6 +170,7 @@ int lsqr_start(eik_lsqr *L, const void *b, eik_stream stream)
 
 int lsqr_iterate(eik_lsqr *L, int iters, int use_graph, eik_stream stream)
 {
+    eik::NvtxRange range("LSQR iterations");
     if (!L || iters < 0) { set_error("bad lsqr_iterate arguments"); return EIK_ERR_INVALID; }
     cudaStream_t st = (cudaStream_t)stream;
     if (use_graph && !L->exec) {

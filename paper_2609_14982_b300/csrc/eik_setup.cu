@@ -934,6 +934,8 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
                   const int *rec_node, int n_rec, const eik_opts *opts, Tangent **out, cudaStream_t st,
                   const double *src_f)
 {
+    NvtxRange range(src_f ? "tangent_build_points" : "tangent_build");
+    NvtxPhase phase;
     *out = nullptr;
     GridDesc g = make_grid_desc(gin);
     const long long N = g.N, SN = N * (long long)S;
@@ -984,6 +986,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
     }
     TRY(cudaMemsetAsync(nid, 0, S * sizeof(unsigned long long), st));
 
+    phase.next("rows");
     // ---- metric, gradient, rows (Sec. 2.2, 3.1, 3.2)
     k_metric<<<blocks_for(N), 256, 0, st>>>(g, gin->xyz, G, nullptr);
     k_grad<<<blocks_for(SN), 256, 0, st>>>(g, S, T, gT);
@@ -991,6 +994,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
                                                t->cs_nat, nid);
     TRY(cudaGetLastError());
 
+    phase.next("trimming");
     // ---- forward and backward trimming (Sec. 3.5, Prop. 2), frontier by frontier
     TRY(sc.get(&act, SN));        // in-degree counters
     TRY(sc.get(&list, SN));       // two frontier queues
@@ -1031,6 +1035,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
         TRY(cudaGetLastError());
     }
 
+    phase.next("SCC of the residual");
     // ---- SCCs of the residual (both closures) by Tarjan's algorithm (Sec. 4.1 [ref50]),
     // one host thread per group of sources: the residual is a few percent of the vertices
     {
@@ -1088,6 +1093,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
     TRY(cudaMemsetAsync(csize, 0, SN * sizeof(int), st));
     k_comp_size<<<blocks_for(SN), 256, 0, st>>>(SN, lab, csize);
 
+    phase.next("levels");
     // ---- canonical levels (longest path on the condensation)
     TRY(sc.get(&lvl, SN));
     TRY(sc.get(&asg, SN));
@@ -1183,6 +1189,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
         return fail(EIK_ERR_INVALID);
     }
 
+    phase.next("canonical order");
     // ---- canonical order: sort by (source, level, component, node)
     unsigned long long *keys, *skeys;
     int *lcount, *head;
@@ -1206,6 +1213,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
     std::vector<int> hl((size_t)S * maxL);
     TRY(cudaMemcpyAsync(hl.data(), lcount, hl.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
 
+    phase.next("canonical rows");
     // ---- rows in canonical order (gather form) and transposed rows
     int *fcnt, *tcnt;
     long long *fscan, *tscan;
@@ -1266,6 +1274,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
                                            t->dn_node, t->dn_w32, t->dn_w64);
     TRY(cudaGetLastError());
 
+    phase.next("coefficients");
     // ---- C*M coefficients, receivers
     TRY(dalloc(&t->cq64, SN));
     TRY(dalloc(&t->cq32, SN));
@@ -1291,6 +1300,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
     }
     k_rec_slot<<<blocks_for(SN), 256, 0, st>>>(SN, N, t->perm, recpos, t->rec_slot);
 
+    phase.next("blocks");
     // ---- level pointers (host) and blocks
     t->level_ptr.assign((size_t)S * (maxL + 1), 0);
     for (int a = 0; a < S; ++a) {
@@ -1360,6 +1370,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
         }
     }
 
+    phase.next("items");
     // ---- traversal work items: level-major over sources
     {
         int chunk = opts->chunk > 0 ? std::min(opts->chunk, ITEM_CAP) : ITEM_MAX;
@@ -1454,6 +1465,7 @@ int build_tangent(const eik_grid *gin, const double *T, const double *s, int S, 
         TRY(cudaStreamSynchronize(st));   // the host vectors above go out of scope
     }
 
+    phase.next("statistics");
     // ---- statistics
     {
         std::vector<unsigned long long> hid(S);

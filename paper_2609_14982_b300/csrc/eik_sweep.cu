@@ -201,6 +201,7 @@ static int sweep_weights(Tangent *t, bool transpose, int dtype, const void **out
 int sweep(Tangent *t, bool transpose, const void *b, int R, void *x, int dtype, const eik_opts *opts, int *cycles,
           cudaStream_t st)
 {
+    NvtxRange range(transpose ? "sweep A^T" : "sweep A");
     if (dtype != EIK_F32 && dtype != EIK_F64) { set_error("bad dtype"); return EIK_ERR_INVALID; }
     if (opts->sweep_max_cycles < 1) { set_error("sweep_max_cycles must be positive"); return EIK_ERR_INVALID; }
     const size_t esz = dtype == EIK_F32 ? 4 : 8;
