@@ -376,6 +376,16 @@ int tangent_tune(eik_tangent *t, const eik_opts *opts);
  */
 int tangent_debug_hold(eik_tangent *t, int source, int step);
 
+/*
+ * tangent_debug_poke_edge -- test hook of the checked build (build.py --checked) only:
+ * overwrites upstream edge `edge` (index into source `source`'s forward rows, canonical
+ * order) with the position `value`, so a test can show that the checked traversal reports
+ * an out-of-range index (EIK_ERR_CUDA from tangent_status, "index out of range") instead of
+ * reading it.  The normal build returns EIK_ERR_INVALID and changes nothing.
+ * Synchronizes the device.
+ */
+int tangent_debug_poke_edge(eik_tangent *t, int source, long long edge, int value);
+
 /* Release everything the tangent owns (waits for its streams). NULL is ignored. */
 void tangent_free(eik_tangent *t);
 

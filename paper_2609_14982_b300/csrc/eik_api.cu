@@ -276,6 +276,10 @@ int tangent_status(eik_tangent *tt, eik_stream stream)
             return EIK_ERR_TIMEOUT;
         }
         if (e[0] == eik::DEV_SINGULAR) { eik::set_error("singular SCC block"); return EIK_ERR_SINGULAR_BLOCK; }
+        if (e[0] == eik::DEV_BAD_INDEX) {
+            eik::set_error("index out of range (checked build): source %d, position %d, value %d", e[1], e[2], e[3]);
+            return EIK_ERR_CUDA;
+        }
         if (e[0] != 0) { eik::set_error("device fault code %d", e[0]); return EIK_ERR_CUDA; }
         return EIK_OK;
     })
@@ -303,6 +307,26 @@ int tangent_tune(eik_tangent *tt, const eik_opts *o)
     t->opts.pass_units = o->pass_units;
     t->opts.block_lu_min = o->block_lu_min;
     return EIK_OK;
+}
+
+int tangent_debug_poke_edge(eik_tangent *tt, int source, long long edge, int value)
+{
+    EIK_GUARD({
+        if (!tt) { eik::set_error("tangent is NULL"); return EIK_ERR_INVALID; }
+#ifndef EIK_CHECKED
+        (void)source; (void)edge; (void)value;
+        eik::set_error("tangent_debug_poke_edge needs the checked build");
+        return EIK_ERR_INVALID;
+#else
+        Tangent *t = tt->impl;
+        if (source < 0 || source >= t->S) { eik::set_error("bad source"); return EIK_ERR_INVALID; }
+        const long long ne = t->ebase[source + 1] - t->ebase[source];
+        if (edge < 0 || edge >= ne) { eik::set_error("edge %lld outside [0, %lld)", edge, ne); return EIK_ERR_INVALID; }
+        EIK_CHECK(cudaDeviceSynchronize());
+        EIK_CHECK(cudaMemcpy(t->up_node + t->ebase[source] + edge, &value, sizeof(int), cudaMemcpyHostToDevice));
+        return EIK_OK;
+#endif
+    })
 }
 
 int tangent_debug_hold(eik_tangent *tt, int source, int step)

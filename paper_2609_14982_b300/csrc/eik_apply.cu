@@ -99,6 +99,31 @@ struct TravParams {
 // all issued before they are summed.
 constexpr int MAX_ROW = 6;   // at most 2 * ndim faces per row
 
+// Checked build (compiled with -DEIK_CHECKED, the library's debug mode in place of a
+// sanitizer): before a position is computed, its node, its row's edge range in the staged
+// arrays, every upstream position and its receiver slot are checked against their arrays;
+// a bad one latches DEV_BAD_INDEX {source, position, value} and the position is skipped.
+// The normal build compiles the check away.
+#ifdef EIK_CHECKED
+__device__ __noinline__ bool position_ok(const TravParams &P, long long a, int pos, int v, int e0, int cnt, int staged,
+                                         const int *en, int rec)
+{
+    long long bad = -1;
+    if (v < 0 || v >= P.N) bad = v;
+    else if (e0 < 0 || cnt < 0 || cnt > MAX_ROW || (staged >= 0 && e0 + cnt > staged)) bad = e0 + cnt;
+    else if (rec >= P.n_rec) bad = rec;
+    else
+        for (int e = 0; e < cnt; ++e)
+            if (en[e0 + e] < 0 || en[e0 + e] >= P.N) { bad = en[e0 + e]; break; }
+    if (bad < 0) return true;
+    if (atomicCAS(P.err, 0, DEV_BAD_INDEX) == 0) { P.err[1] = (int)a; P.err[2] = pos; P.err[3] = (int)bad; }
+    return false;
+}
+#define EIK_POSITION_OK(P, a, pos, v, e0, cnt, staged, en, rec) position_ok(P, a, pos, v, e0, cnt, staged, en, rec)
+#else
+#define EIK_POSITION_OK(P, a, pos, v, e0, cnt, staged, en, rec) true
+#endif
+
 template <typename T> struct Stage {
     int perm[ITEM_MAX];
     int rec[ITEM_MAX];
@@ -328,6 +353,7 @@ __device__ void run_block(const TravParams &P, int a, int b, int tid = threadIdx
         const int v = ~__ldg(perm + p);
         double acc;
         const int rec = P.rec_slot[a * N + p];
+        if (!EIK_POSITION_OK(P, a, p, v, rp[p], rp[p + 1] - rp[p], -1, en, rec)) continue;
         if (!TR) {
             if (P.mode == MODE_J)
                 acc = P.cq64[a * N + p] * (double)in[((P.shared_in ? 0 : (long long)a * N) + v) * P.ld_in + r];
@@ -603,6 +629,7 @@ __device__ __forceinline__ void run_stage_singletons(const TravParams &P, const 
         if (v < 0) continue;      // member of a nontrivial block
         const int e0 = S.rp[k] - S.ebx, cnt = S.rp[k + 1] - S.rp[k];
         const int rec = S.rec[k];
+        if (!EIK_POSITION_OK(P, a, p0 + k, v, e0, cnt, S.eby - S.ebx, S.en, rec)) continue;
         const T c = S.cq[k];
         const bool has_in = !(TR && P.mode == MODE_J && rec < 0);
         const T scale = (!TR && P.mode == MODE_J) ? c : T(1);
@@ -667,6 +694,11 @@ __device__ __forceinline__ void run_stage_lanes(const TravParams &P, const ItemS
             if (node[q] < 0) continue;
             e0[q] = S.rp[k] - S.ebx;
             cnt[q] = S.rp[k + 1] - S.rp[k];
+            if (!EIK_POSITION_OK(P, a, p0 + k, node[q], e0[q], cnt[q], S.eby - S.ebx, S.en, S.rec[k])) {
+                node[q] = -1;
+                cnt[q] = 0;
+                continue;
+            }
 #pragma unroll
             for (int e = 0; e < 3; ++e)
                 if (e < cnt[q]) {

@@ -13,7 +13,8 @@ import os
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libeik.so")
+# EIK_LIB selects another build of the library, e.g. the checked build (build.py --checked)
+LIB_PATH = os.environ.get("EIK_LIB") or os.path.join(HERE, "libeik.so")
 
 EIK_F64, EIK_F32 = 0, 1
 MODEL_SLOWNESS, MODEL_VELOCITY, MODEL_RELATIVE = 0, 1, 2
@@ -30,7 +31,7 @@ EXPORTED = ["eik_opts_default", "eik_last_error", "eik_version", "eik_forward", 
             "gn_lsmr_solution", "gn_free", "model_cells_to_nodes", "model_nodes_to_cells",
             "tangent_set_receivers", "tangent_apply_interp", "tangent_apply_interp_T", "gn_create_cells", "gn_rhs",
             "tangent_apply_batch", "tangent_apply_T_batch", "eik_forward_points", "tangent_build_points",
-            "eik_forward_warm"]
+            "eik_forward_warm", "tangent_debug_poke_edge"]
 
 
 class EikError(RuntimeError):
@@ -94,6 +95,7 @@ def lib():
         L.tangent_free.argtypes = [P]
         L.tangent_free.restype = None
         L.tangent_debug_hold.argtypes = [P, I, I]
+        L.tangent_debug_poke_edge.argtypes = [P, I, C.c_longlong, I]
         L.tangent_tune.argtypes = [P, C.POINTER(Opts)]
         L.lsqr_create.argtypes = [P, I, C.POINTER(P)]
         L.lsqr_start.argtypes = [P, P, P]
@@ -402,6 +404,10 @@ class Tangent:
                 raise KeyError(k)
             setattr(self.opts, k, v)
         _check(lib().tangent_tune(self.h, C.byref(self.opts)))
+
+    def debug_poke_edge(self, source: int, edge: int, value: int):
+        """Test hook of the checked build: overwrite one upstream edge's position."""
+        _check(lib().tangent_debug_poke_edge(self.h, source, edge, value))
 
     def debug_hold(self, source: int, step: int):
         """Test hook: make the persistent traversal's wait before (source, step) run out."""
