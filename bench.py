@@ -174,7 +174,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_state = time.time() - t0
     sched = {"persistent": eik.SCHED_PERSISTENT, "levels": eik.SCHED_LEVELS, "staged": eik.SCHED_STAGED,
-             "cluster": eik.SCHED_CLUSTER}[args.schedule]
+             "cluster": eik.SCHED_CLUSTER, "sync": eik.SCHED_SYNC}[args.schedule]
     opts = eik.default_opts(schedule=sched, item_deps=0 if args.level_waits else 1, ctas_per_sm=args.ctas_per_sm,
                             cluster_size=args.cluster_size, cluster_threads=args.cluster_threads,
                             pass_units=args.pass_units, split_dirs=int(args.split_dirs))
@@ -202,7 +202,7 @@ def run_ours(args):
         for c in tuned["tried"]:
             c["ms"] = round(c["ms"], 3)
         names = {eik.SCHED_PERSISTENT: "persistent", eik.SCHED_LEVELS: "levels", eik.SCHED_STAGED: "staged",
-                 eik.SCHED_CLUSTER: "cluster"}
+                 eik.SCHED_CLUSTER: "cluster", eik.SCHED_SYNC: "sync"}
         schedule = names[rec["setting"]["schedule"]]
         pass_units = rec["setting"].get("pass_units", 0)
     gen = torch.Generator(dev).manual_seed(20263 + rank)
@@ -981,7 +981,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--schedule", choices=["persistent", "levels", "staged", "cluster"], default="persistent")
+    ap.add_argument("--schedule", choices=["persistent", "levels", "staged", "cluster", "sync"], default="persistent")
     ap.add_argument("--state-cycles", type=int, default=0,
                     help="--workload state: only the 3-D apply grid (FP32 far field) for this many cycles (profiling)")
     ap.add_argument("--split-dirs", action="store_true",

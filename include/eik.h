@@ -61,9 +61,15 @@ typedef enum {
                                       memory by per-thread async copies (needs R x element size a
                                       multiple of 16 bytes, >= 64, items x 16-byte lanes <= 512
                                       and the two stages within 200 KB; else as LEVELS) */
-    EIK_SCHED_CLUSTER = 3          /* one launch; a thread-block cluster owns one source at a time
+    EIK_SCHED_CLUSTER = 3,         /* one launch; a thread-block cluster owns one source at a time
                                       and walks its levels with one hardware cluster barrier per
                                       level (no device-side spin waits) */
+    EIK_SCHED_SYNC = 4             /* one cooperative launch (all CTAs resident); every source
+                                      advances one level per global step and the steps end at a
+                                      bounded grid-wide barrier; an SCC block takes two steps of
+                                      its source (right-hand side, then the inverse product spread
+                                      over the grid); needs block_lu_min = 0 and holds the whole
+                                      GPU, so two such traversals do not overlap */
 } eik_schedule;
 
 typedef struct {
@@ -109,7 +115,9 @@ typedef struct {
     int cluster_threads;       /* threads per CTA, a multiple of 32 in 64..256 (default 0 = 256) */
     int pass_units;            /* most right-hand-side vectors a thread of the cluster schedule
                                   carries for one position: 1, 2 or 4 (default 0 = 4); a thread
-                                  carries 4 / that many positions per round */
+                                  carries 4 / that many positions per round.  Level-synchronous
+                                  schedule: rows a thread has in flight, 0 = 1 (1024 threads per
+                                  CTA), 2 (768 threads), 4 (512 threads) */
     /* SCC block solves */
     int block_lu_min;          /* blocks of at least this many nodes are solved by FP64 forward and
                                   back substitution with their partial-pivot LU factors (one warp
@@ -361,6 +369,10 @@ int tangent_status(eik_tangent *t, eik_stream stream);
  * rhs_chunk, wait_timeout_s, item_deps, cluster_size, cluster_threads, pass_units,
  * block_lu_min and split_dirs are taken from opts (structure options are ignored).
  * Turning split_dirs on allocates the transpose's counters (synchronizes the device).
+ * The level-synchronous schedule builds its step tables (about 48 bytes per row and
+ * direction for FP32 traversals, 64 for FP64) at its first traversal of each precision,
+ * which synchronizes the device and must not happen inside a stream capture: run one
+ * traversal of that precision before capturing (the Krylov solvers' start calls do).
  * Used by the autotuner; affects later calls only.
  */
 int tangent_tune(eik_tangent *t, const eik_opts *opts);

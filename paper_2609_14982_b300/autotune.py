@@ -5,11 +5,13 @@ module times one J p and one J^T y (CUDA events on the current stream) for each
 candidate run-time setting and applies the fastest with tangent_tune, caching the choice
 per (grid size, sources, levels, R, dtype) in a JSON file.  The knobs:
   schedule           persistent item queue, cluster (one cluster per source, a hardware
-                     barrier per level) or graph-replayed per-level launches;
+                     barrier per level), level-synchronous (one cooperative launch, a
+                     grid-wide barrier per global step) or graph-replayed per-level launches;
   rhs_chunk          right-hand-side columns per traversal pass;
   threads per level  cluster schedule: cluster_size CTAs x cluster_threads threads work on
                      one source's level; persistent schedule: CTAs per SM (ctas_per_sm);
-  lane groups        pass_units: right-hand-side vectors a thread carries per position;
+  lane groups        pass_units: right-hand-side vectors a thread carries per position
+                     (level-synchronous schedule: rows a thread has in flight, 1, 2 or 4);
   block tiling       block_lu_min: SCC blocks of at least this size are solved by
                      column-parallel substitution with the LU factors instead of the
                      explicit inverse;
@@ -59,6 +61,8 @@ def candidates(R: int, dtype) -> list:
                 for pu in (2, 4):
                     out.append({"schedule": eik.SCHED_CLUSTER, "rhs_chunk": ch, "cluster_size": cs,
                                 "cluster_threads": ct, "pass_units": pu})
+        for pu in (0, 2, 4):
+            out.append({"schedule": eik.SCHED_SYNC, "rhs_chunk": ch, "pass_units": pu})
         for blk in (0, 64):
             out.append({"schedule": eik.SCHED_PERSISTENT, "rhs_chunk": ch, "block_lu_min": blk})
         for per_sm in (1, 2):
@@ -78,6 +82,7 @@ def quick_candidates(R: int, dtype) -> list:
            dict(base, schedule=eik.SCHED_PERSISTENT, block_lu_min=64),
            dict(base, schedule=eik.SCHED_CLUSTER),
            dict(base, schedule=eik.SCHED_CLUSTER, cluster_size=8, pass_units=2),
+           dict(base, schedule=eik.SCHED_SYNC, pass_units=4),
            dict(base, schedule=eik.SCHED_LEVELS)]
     return out
 

@@ -227,6 +227,13 @@ struct Tangent {
     PointData pts;
     // the transpose direction's own launch state (opts.split_dirs)
     Lane lane_t;
+    // level-synchronous schedule (eik_sync.cu), per direction (forward, transpose): the unit
+    // records in step order per precision (FP32, FP64) and per step its first record and
+    // singleton records; the grid-barrier counters (32 words per direction)
+    void *sync_rec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int *sync_base[2] = {nullptr, nullptr};
+    int sync_steps[2] = {0, 0};
+    unsigned *sync_bar = nullptr;
 };
 
 // whether the transpose direction runs on its own launch state
@@ -235,6 +242,9 @@ inline bool split_lane(const Tangent *t, bool TR) { return TR && t->opts.split_d
 inline void *lane_ws(const Tangent *t, bool TR) { return split_lane(t, TR) ? t->lane_t.ws_vec : t->ws_vec; }
 // allocate the transpose's counters and ticket (once)
 int enable_split(Tangent *t);
+// build the level-synchronous schedule's step tables of a precision (EIK_F32, EIK_F64, or -1 for
+// both) and its barrier counters (once; synchronizes)
+int prepare_sync(Tangent *t, int dtype);
 
 // src_f (host [S][ndim] fractional logical coordinates) selects point sources; then
 // src_node is ignored

@@ -18,7 +18,7 @@ LIB_PATH = os.environ.get("EIK_LIB") or os.path.join(HERE, "libeik.so")
 
 EIK_F64, EIK_F32 = 0, 1
 MODEL_SLOWNESS, MODEL_VELOCITY, MODEL_RELATIVE = 0, 1, 2
-SCHED_PERSISTENT, SCHED_LEVELS, SCHED_STAGED, SCHED_CLUSTER = 0, 1, 2, 3
+SCHED_PERSISTENT, SCHED_LEVELS, SCHED_STAGED, SCHED_CLUSTER, SCHED_SYNC = 0, 1, 2, 3, 4
 STATUS = {0: "OK", -1: "INVALID", -2: "OOM", -3: "SINGULAR_BLOCK", -4: "NOT_CONVERGED", -5: "TIMEOUT",
           -6: "CUDA", -7: "CYCLE"}
 
