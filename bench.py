@@ -88,16 +88,28 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+KERNEL_SOURCES = ("eik_apply.cu", "eik_trav.h", "eik_vec.cuh")   # the files that define the traversal kernels
+
+
+def kernel_source_digest() -> str:
+    """SHA-256 over the traversal kernels' source files (those present), in a fixed order."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        path = os.path.join(ROOT, "paper_2609_14982_b300", "csrc", name)
+        if os.path.exists(path):
+            h.update(open(path, "rb").read())
+    return h.hexdigest()
+
+
 def measured_traffic(direction: str, kernel: str) -> float | None:
     """DRAM bytes per node-update of the traversal kernel from the committed ncu summary
     (profiles/traffic.txt: one line per kernel and direction with the SHA-256 of the
-    kernel source it was captured from); None once the kernel source has changed since
-    the capture."""
-    import hashlib
+    kernel sources it was captured from, kernel_source_digest); None once the kernel
+    source has changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
-    src = os.path.join(ROOT, "paper_2609_14982_b300", "csrc", "eik_apply.cu")
     try:
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        digest = kernel_source_digest()
         for line in open(path):
             if line.startswith("#") or not line.strip():
                 continue

@@ -37,9 +37,12 @@ def test_algorithmic_bytes_closed_form(bench):
 
 def test_traffic_record_requires_matching_source_hash(bench, tmp_path, monkeypatch):
     """measured_traffic reads profiles/traffic.txt only for the kernel and direction it
-    names and only while eik_apply.cu still hashes to the recorded value."""
-    src = os.path.join(ROOT, "paper_2609_14982_b300", "csrc", "eik_apply.cu")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    names and only while the traversal kernels' sources still hash to the recorded value."""
+    h = hashlib.sha256()
+    for name in ("eik_apply.cu", "eik_trav.h", "eik_vec.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2609_14982_b300", "csrc", name), "rb").read())
+    digest = h.hexdigest()
+    assert bench.kernel_source_digest() == digest
     got = bench.measured_traffic("fwd", "k_traverse_persistent<float,4,false>")
     rec = open(os.path.join(ROOT, "profiles", "traffic.txt")).read()
     if digest in rec:
