@@ -201,7 +201,7 @@ def run_ours(args):
     st = [tan.stats(a) for a in range(S)]
 
     dtype = torch.float32
-    schedule, pass_units, tuned = args.schedule, args.pass_units, None
+    schedule, pass_units, tuned, item_slots = args.schedule, args.pass_units, None, 0
     if args.autotune:
         # time each schedule's default and a few variants on this tangent (one J p + J^T y
         # pair each, CUDA events) and keep the fastest for the timed region
@@ -209,7 +209,8 @@ def run_ours(args):
         rec = autotune(tan, R, dtype, reps=3, cache_path=None, cands=quick_candidates(R, dtype), seed=rank)
         tuned = {"setting": rec["setting"], "ms": round(rec["ms"], 3), "tune_s": round(rec["tune_s"], 2),
                  "tried": [{k: v for k, v in c.items() if k in ("ms", "schedule", "pass_units", "block_lu_min",
-                                                                 "cluster_size", "split_dirs", "ctas_per_sm")}
+                                                                 "cluster_size", "split_dirs", "ctas_per_sm",
+                                                                 "item_slots")}
                            for c in rec["tried"]]}
         for c in tuned["tried"]:
             c["ms"] = round(c["ms"], 3)
@@ -217,6 +218,7 @@ def run_ours(args):
                  eik.SCHED_CLUSTER: "cluster", eik.SCHED_SYNC: "sync"}
         schedule = names[rec["setting"]["schedule"]]
         pass_units = rec["setting"].get("pass_units", 0)
+        item_slots = rec["setting"].get("item_slots", 0)
     gen = torch.Generator(dev).manual_seed(20263 + rank)
     p = torch.randn((N, R), device=dev, dtype=dtype, generator=gen)
     y = torch.randn((S, n_rec, R), device=dev, dtype=dtype, generator=gen)
@@ -401,7 +403,10 @@ def run_ours(args):
     kname = {"persistent": "k_traverse_persistent<float,4,%s>" if pass_units <= 1 else
                            "k_traverse_persistent<float,4,%s," + str(min(pass_units, 4)) + ",1>",
              "levels": "k_traverse_level<float,4,%s,1>", "staged": "k_traverse_staged<float,4,%s>",
-             "cluster": "k_traverse_cluster<float,4,%s," + str(pass_units or 4) + ">"}[schedule]
+             "cluster": "k_traverse_cluster<float,4,%s," + str(pass_units or 4) + ">",
+             "sync": "k_traverse_sync<float,4,%s>"}[schedule]
+    if schedule == "persistent" and item_slots >= 2 and pass_units <= 1:
+        kname = "k_traverse_multi<float,4,%s," + str(min(item_slots, 4)) + ">"
     kname = kname % ("false" if dom == "fwd" else "true")
     tpu = measured_traffic(dom, kname)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -462,7 +467,7 @@ def run_ours(args):
                 "ms_per_step": round(e2e_ms, 4),
                 "copies": "every step: p and y from pinned host memory, d_rec and g back; double-buffered on two "
                           "copy streams, overlapping the neighbouring steps' traversals"},
-        "gpu_launches": args.steps * (3 if schedule in ("persistent", "cluster") else (2 * max(x["levels"] for x in st) + 3)),
+        "gpu_launches": args.steps * (3 if schedule in ("persistent", "cluster", "sync") else (2 * max(x["levels"] for x in st) + 3)),
         "clocks": clocks,
         "sweep_baseline": sweep,
         "setup": {"eik_forward_s": round(t_state, 3), "eik_cycles": cyc, "tangent_build_s": round(t_setup, 3),

@@ -133,6 +133,11 @@ typedef struct {
                                   calls (interp forms, solves, sweeping) still must not overlap.
                                   0 (default): calls on one tangent must not overlap on the
                                   device */
+    int item_slots;            /* persistent schedule: work items a CTA holds at once, 1 (default)
+                                  or 2..4; with several, each item's structure lands in its own
+                                  shared-memory slot and the CTA computes whichever held item
+                                  has its upstream items done first (64-position items, one
+                                  right-hand-side vector per thread) */
 } eik_opts;
 
 typedef struct {
@@ -367,7 +372,8 @@ int tangent_status(eik_tangent *t, eik_stream stream);
 /*
  * tangent_tune -- replace the run-time options of a built tangent: schedule, ctas_per_sm,
  * rhs_chunk, wait_timeout_s, item_deps, cluster_size, cluster_threads, pass_units,
- * block_lu_min and split_dirs are taken from opts (structure options are ignored).
+ * block_lu_min, split_dirs and item_slots are taken from opts (structure options are
+ * ignored).
  * Turning split_dirs on allocates the transpose's counters (synchronizes the device).
  * The level-synchronous schedule builds its step tables (about 48 bytes per row and
  * direction for FP32 traversals, 64 for FP64) at its first traversal of each precision,

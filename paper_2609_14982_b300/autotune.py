@@ -17,7 +17,8 @@ per (grid size, sources, levels, R, dtype) in a JSON file.  The knobs:
                      explicit inverse;
   waits              per-item dependencies or whole previous level (persistent);
   concurrency        split_dirs: J p and J^T y on two streams at once, each with about
-                     half the CTAs (the pair is timed that way).
+                     half the CTAs (the pair is timed that way);
+  items in flight    item_slots: work items a CTA of the persistent schedule holds at once.
 """
 from __future__ import annotations
 
@@ -34,7 +35,7 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "eik_autotune.js
 
 # every knob at its default: a candidate names only what it changes
 DEFAULTS = {"schedule": eik.SCHED_PERSISTENT, "rhs_chunk": 0, "ctas_per_sm": 0, "item_deps": 1, "pass_units": 0,
-            "cluster_size": 0, "cluster_threads": 0, "block_lu_min": 0, "split_dirs": 0}
+            "cluster_size": 0, "cluster_threads": 0, "block_lu_min": 0, "split_dirs": 0, "item_slots": 0}
 
 
 def _key(tan, R: int, dtype) -> str:
@@ -67,6 +68,10 @@ def candidates(R: int, dtype) -> list:
             out.append({"schedule": eik.SCHED_PERSISTENT, "rhs_chunk": ch, "block_lu_min": blk})
         for per_sm in (1, 2):
             out.append({"schedule": eik.SCHED_PERSISTENT, "rhs_chunk": ch, "split_dirs": 1, "ctas_per_sm": per_sm})
+        for slots in (2, 3):
+            out.append({"schedule": eik.SCHED_PERSISTENT, "rhs_chunk": ch, "item_slots": slots})
+            out.append({"schedule": eik.SCHED_PERSISTENT, "rhs_chunk": ch, "item_slots": slots, "split_dirs": 1,
+                        "ctas_per_sm": 2})
     return out
 
 
@@ -75,9 +80,11 @@ def quick_candidates(R: int, dtype) -> list:
     each schedule, the cluster schedule at two sizes, and the lane-group and
     block-tiling variants of the persistent schedule."""
     base = {"rhs_chunk": 0, "ctas_per_sm": 0, "item_deps": 1, "pass_units": 0, "cluster_size": 0,
-            "cluster_threads": 0, "block_lu_min": 0, "split_dirs": 0}
+            "cluster_threads": 0, "block_lu_min": 0, "split_dirs": 0, "item_slots": 0}
     out = [dict(base, schedule=eik.SCHED_PERSISTENT),
            dict(base, schedule=eik.SCHED_PERSISTENT, split_dirs=1, ctas_per_sm=2),
+           dict(base, schedule=eik.SCHED_PERSISTENT, split_dirs=1, ctas_per_sm=2, item_slots=2),
+           dict(base, schedule=eik.SCHED_PERSISTENT, item_slots=2),
            dict(base, schedule=eik.SCHED_PERSISTENT, pass_units=2),
            dict(base, schedule=eik.SCHED_PERSISTENT, block_lu_min=64),
            dict(base, schedule=eik.SCHED_CLUSTER),

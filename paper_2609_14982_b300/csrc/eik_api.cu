@@ -289,7 +289,8 @@ int tangent_tune(eik_tangent *tt, const eik_opts *o)
 {
     if (!tt || !o) { eik::set_error("bad tangent_tune arguments"); return EIK_ERR_INVALID; }
     if (o->schedule < EIK_SCHED_PERSISTENT || o->schedule > EIK_SCHED_SYNC) { eik::set_error("bad schedule"); return EIK_ERR_INVALID; }
-    if (o->rhs_chunk < 0 || o->ctas_per_sm < 0 || !(o->wait_timeout_s > 0) || o->block_lu_min < 0) { eik::set_error("bad tuning values"); return EIK_ERR_INVALID; }
+    if (o->rhs_chunk < 0 || o->ctas_per_sm < 0 || !(o->wait_timeout_s > 0) || o->block_lu_min < 0 || o->item_slots < 0 ||
+        o->item_slots > 4) { eik::set_error("bad tuning values"); return EIK_ERR_INVALID; }
     Tangent *t = tt->impl;
     if (o->split_dirs) {
         int rc = EIK_OK;
@@ -306,6 +307,7 @@ int tangent_tune(eik_tangent *tt, const eik_opts *o)
     t->opts.cluster_threads = o->cluster_threads;
     t->opts.pass_units = o->pass_units;
     t->opts.block_lu_min = o->block_lu_min;
+    t->opts.item_slots = o->item_slots;
     return EIK_OK;
 }
 

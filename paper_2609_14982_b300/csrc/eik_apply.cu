@@ -1304,6 +1304,159 @@ __global__ void __launch_bounds__(256, 2) k_traverse_cluster(const __grid_consta
         }
 }
 
+// ---------------------------------------------------------------- multi-slot persistent schedule
+// The persistent schedule with NS work items held by each CTA at once.  Every held item's
+// structure and dependency list is copied into its own shared-memory slot with cp.async,
+// and each thread's copies signal the slot's mbarrier (cp.async.mbarrier.arrive), so warp 0
+// can see without waiting which slots have landed.  Warp 0 then polls the dependencies of
+// every landed item in one round (one flag per lane) and hands the CTA the lowest-ticket
+// item that is ready; a CTA that waited on one item in the single-slot schedule now
+// computes another.  The computed slot takes the next ticket (taken during the compute)
+// and its copies are issued behind it.  Progress: the lowest unfinished ticket has all
+// its upstream items (lower tickets) done and its copies land unconditionally, so its
+// CTA, which re-polls every held slot each round, picks it in bounded time.  Input rows
+// are read in place (no tile) and prefetched into L2 once the slot's structure is in.
+__device__ __forceinline__ void cp_async_mbar_arrive(unsigned long long *b)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long *b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// input rows of a landed slot into L2 (lanes of warp 0)
+template <typename T, bool TR>
+__device__ __forceinline__ void prefetch_inputs(const TravParams &P, const ItemStage<T> &S, int lane)
+{
+    if (S.it.z < 0) return;
+    const int np = S.it.w - S.it.z;
+    const int rowb = P.R * (int)sizeof(T);
+    for (int k = lane; k < np; k += 32) {
+        const int v = S.perm[k];
+        if (v < 0) continue;
+        const T *src = input_row<T, TR>(P, S.it.x, v, S.rec[k]);
+        if (src)
+            for (int o = 0; o < rowb; o += 128) prefetch_l2(reinterpret_cast<const char *>(src) + o);
+    }
+}
+
+template <typename T, int V, bool TR, int NS>
+__global__ void __launch_bounds__(256, 4) k_traverse_multi(TravParams P, int G)
+{
+    __shared__ ItemStage<T> stg[NS];
+    __shared__ __align__(8) unsigned long long bar[NS];
+    __shared__ int s_pick, s_t;
+    const int tid = threadIdx.x;
+    const int nitems = P.nitems;
+    const unsigned FULL = 0xffffffffu;
+    unsigned ph = 0;                 // bit k: parity of the phase slot k's current copies complete
+    unsigned hinted = 0;             // warp 0: bit k set once slot k's input rows were prefetched
+    if (tid == 0) {
+        for (int k = 0; k < NS; ++k) mbar_init(&bar[k], blockDim.x);
+        for (int k = 0; k < NS; ++k) load_desc(P, stg[k], atomicAdd(P.ticket, 1));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        if (stg[k].idx < nitems) issue_structure<T>(P, stg[k]);
+        cp_async_mbar_arrive(&bar[k]);
+    }
+    for (;;) {
+        // ---- warp 0: the lowest-ticket held item whose copies landed and whose upstream
+        // items are done (-1: nothing held, or a fault)
+        if (tid < 32) {
+            int pick = -1;
+            const unsigned long long t0 = global_ns();
+            for (int round = 0;; ++round) {
+                unsigned held = 0, landed = 0;
+#pragma unroll
+                for (int k = 0; k < NS; ++k)
+                    if (stg[k].idx < nitems) {
+                        held |= 1u << k;
+                        if (mbar_test(&bar[k], (ph >> k) & 1)) landed |= 1u << k;
+                    }
+                if (!held) break;
+                // one dependency flag per lane: slots in order, each its list (or its level counter)
+                unsigned bad = 0;
+                int base = 0;                           // pair index of slot k's first flag
+#pragma unroll
+                for (int k = 0; k < NS; ++k) {
+                    if (!((landed >> k) & 1)) continue;
+                    const ItemStage<T> &S = stg[k];
+                    if (S.it.y == 0) continue;          // first step: nothing upstream
+                    const int nd = S.nd;
+                    const int cnt = nd < 0 ? 1 : nd;
+                    for (int j = ((tid - base) % 32 + 32) % 32; j < cnt; j += 32) {
+                        bool ok;
+                        if (nd < 0) {
+                            const long long c = (long long)S.it.x * P.maxL + S.it.y - 1;
+                            ok = ld_acquire(P.done + c) >= P.item_cnt[c];
+                        } else {
+                            ok = ld_acquire(P.item_done + S.deps[j]) >= 1;
+                        }
+                        if (!ok) bad |= 1u << k;
+                    }
+                    base += cnt;
+                }
+                bad = __reduce_or_sync(FULL, bad);
+                const unsigned ready = landed & ~bad;
+                if (ready) {
+                    int best = -1;
+#pragma unroll
+                    for (int k = 0; k < NS; ++k)
+                        if (((ready >> k) & 1) && (best < 0 || stg[k].idx < stg[best].idx)) best = k;
+                    pick = best;
+                    break;
+                }
+                // slots whose structure landed: their input rows into L2 while waiting
+                const unsigned fresh = landed & ~hinted;
+#pragma unroll
+                for (int k = 0; k < NS; ++k)
+                    if ((fresh >> k) & 1) prefetch_inputs<T, TR>(P, stg[k], tid);
+                hinted |= fresh;
+                int stop = 0;
+                if (tid == 0 && (round & 15) == 15) {
+                    if (*(volatile int *)P.err != 0) stop = 1;
+                    else if (global_ns() - t0 > P.timeout_ns) {
+                        if (atomicCAS(P.err, 0, DEV_TIMEOUT) == 0) { P.err[1] = -1; P.err[2] = -1; P.err[3] = -1; }
+                        stop = 1;
+                    }
+                }
+                if (__shfl_sync(FULL, stop, 0)) break;
+                __nanosleep(32);
+            }
+            if (tid == 0) s_pick = pick;
+        }
+        __syncthreads();             // (A) the picked item's upstream rows are complete
+        const int b = s_pick;
+        if (b < 0) break;
+        ItemStage<T> &C = stg[b];
+        const int4 it = C.it;
+        const int i = C.idx;
+        if (tid == 1) s_t = atomicAdd(P.ticket, 1);
+        if (it.z >= 0) run_stage_singletons<T, V, TR>(P, C, nullptr, G);
+        else run_block<T, TR>(P, it.x, ~it.z);
+        __syncthreads();             // (B) every row of the item written
+        if (tid == 32) {
+            fence_acq_rel_gpu();
+            atomicAdd(P.done + (long long)it.x * P.maxL + it.y, 1);
+            st_relaxed(P.item_done + i, 1);
+        }
+        if (tid == 1) load_desc(P, C, s_t);
+        ph ^= 1u << b;
+        hinted &= ~(1u << b);
+        __syncthreads();             // (C) the slot's next descriptor visible
+        if (C.idx < nitems) issue_structure<T>(P, C);
+        cp_async_mbar_arrive(&bar[b]);
+    }
+    cp_async_wait<0>();              // copies of slots never computed land before the CTA exits
+}
+
 // g[j][r] = sum_a cq_a[j] lam_a[j][r] in source order.  FP64 path: FP64 products and
 // sum.  FP32 path: FP32 products with a compensated (Kahan) FP32 sum, so the rounding
 // error does not grow with the number of sources (B300's FP64 rate would make an FP64
@@ -1702,6 +1855,25 @@ static int launch_traverse(Tangent *t, TravParams &P, int G, cudaStream_t st)
     // item is bound by dependent-instruction and memory latency, not by instruction count)
     const int lanes = P.R / V;
     const int want = t->opts.pass_units > 0 ? t->opts.pass_units : 1;
+    if (t->opts.item_slots >= 2 && t->item_max <= ITEM_MAX && want <= 1) {
+        // several items held per CTA (input rows read in place, prefetched into L2)
+        void (*mk)(TravParams, int) = t->opts.item_slots >= 4 ? k_traverse_multi<T, V, TR, 4>
+                                      : t->opts.item_slots == 3 ? k_traverse_multi<T, V, TR, 3>
+                                                                : k_traverse_multi<T, V, TR, 2>;
+        int per_sm = t->opts.ctas_per_sm;
+        if (per_sm <= 0) {
+            EIK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mk, threads, 0));
+            per_sm = std::max(per_sm, 1);
+        }
+        long long grid = std::min<long long>((long long)t->num_sms * per_sm, P.nitems);
+        grid = std::max<long long>(grid, 1);
+        EIK_CHECK(cudaMemsetAsync(P.done, 0, (size_t)t->S * t->maxL * sizeof(int), st));
+        EIK_CHECK(cudaMemsetAsync(P.ticket, 0, sizeof(int), st));
+        EIK_CHECK(cudaMemsetAsync(P.item_done, 0, (size_t)std::max(P.nitems, 1) * sizeof(int), st));
+        mk<<<(unsigned)grid, threads, 0, st>>>(P, G);
+        EIK_CHECK_LAUNCH();
+        return EIK_OK;
+    }
     void (*kern)(TravParams, int, int) = k_traverse_persistent<T, V, TR>;
     if (t->item_max > ITEM_MAX) kern = k_traverse_persistent<T, V, TR, 0, 1, ITEM_CAP>;   // large items (R small)
     else if (want >= 4 && lanes % 4 == 0 && lanes / 4 <= threads) kern = k_traverse_persistent<T, V, TR, 4, 1>;

@@ -51,7 +51,7 @@ class Opts(C.Structure):
                 ("sweep_tol", C.c_double), ("sweep_max_cycles", C.c_int), ("rhs_chunk", C.c_int),
                 ("eik_fp32", C.c_int), ("eik_fp64_radius", C.c_double), ("item_deps", C.c_int),
                 ("cluster_size", C.c_int), ("cluster_threads", C.c_int), ("pass_units", C.c_int),
-                ("block_lu_min", C.c_int), ("split_dirs", C.c_int)]
+                ("block_lu_min", C.c_int), ("split_dirs", C.c_int), ("item_slots", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -397,10 +397,10 @@ class Tangent:
 
     def tune(self, **kw):
         """Change run-time options (schedule, ctas_per_sm, rhs_chunk, wait_timeout_s, item_deps,
-        cluster_size, cluster_threads, pass_units, block_lu_min, split_dirs)."""
+        cluster_size, cluster_threads, pass_units, block_lu_min, split_dirs, item_slots)."""
         for k, v in kw.items():
             if k not in ("schedule", "ctas_per_sm", "rhs_chunk", "wait_timeout_s", "item_deps", "cluster_size",
-                         "cluster_threads", "pass_units", "block_lu_min", "split_dirs"):
+                         "cluster_threads", "pass_units", "block_lu_min", "split_dirs", "item_slots"):
                 raise KeyError(k)
             setattr(self.opts, k, v)
         _check(lib().tangent_tune(self.h, C.byref(self.opts)))
