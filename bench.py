@@ -189,7 +189,7 @@ def run_ours(args):
              "cluster": eik.SCHED_CLUSTER, "sync": eik.SCHED_SYNC}[args.schedule]
     opts = eik.default_opts(schedule=sched, item_deps=0 if args.level_waits else 1, ctas_per_sm=args.ctas_per_sm,
                             cluster_size=args.cluster_size, cluster_threads=args.cluster_threads,
-                            pass_units=args.pass_units, split_dirs=int(args.split_dirs))
+                            pass_units=args.pass_units, split_dirs=int(args.split_dirs), item_slots=args.item_slots)
     if args.split_dirs and not args.ctas_per_sm:
         opts.ctas_per_sm = 2
     if args.chunk:
@@ -201,7 +201,7 @@ def run_ours(args):
     st = [tan.stats(a) for a in range(S)]
 
     dtype = torch.float32
-    schedule, pass_units, tuned, item_slots = args.schedule, args.pass_units, None, 0
+    schedule, pass_units, tuned, item_slots = args.schedule, args.pass_units, None, args.item_slots
     if args.autotune:
         # time each schedule's default and a few variants on this tangent (one J p + J^T y
         # pair each, CUDA events) and keep the fastest for the timed region
@@ -1043,6 +1043,7 @@ def main():
     ap.add_argument("--cluster-threads", type=int, default=0, help="cluster schedule: threads per CTA (0 = 256)")
     ap.add_argument("--pass-units", type=int, default=0, help="cluster schedule: units per thread per round (2 or 4)")
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--item-slots", type=int, default=0, help="persistent schedule: work items held per CTA (2..4)")
     ap.add_argument("--chunk", type=int, default=0, help="positions per work item (default: the library's, 64)")
     ap.add_argument("--level-waits", action="store_true",
                     help="persistent items wait for their whole previous level, not only their upstream items")
