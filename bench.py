@@ -627,9 +627,10 @@ def run_gn(args):
 def stress_config5(steps: int = 3, check_oracle: bool = True, sweep: bool = True) -> dict:
     """Config 5, the uneven-batch stress case: three steep-hill grids (slopes up to about
     55 deg) -- 101x101x51 (32 sources, R = 8), 161x121x61 (32, R = 32), 201x201x101 (64,
-    R = 128) -- traversed together: J p of all three grids in ONE launch of the cluster
-    schedule and J^T y (summed over sources) in one more (tangent_apply_batch), with every
-    tangent's workspace holding all its right-hand sides.  Per grid: the error of J p and
+    R = 128) -- traversed together: J p of all three grids in ONE persistent launch (the
+    work items of all three in one merged step-major order, two items held per CTA) and
+    J^T y (summed over sources) in one more (tangent_apply_batch), with every tangent's
+    workspace holding all its right-hand sides.  Per grid: the error of J p and
     J^T y against the FP64 oracle on a sampled source and four columns (the oracle builds
     its tangent from the same state), and the node-updates/s of BTF against GPU
     directional sweeping on a 4-source slice of the grid at R = min(R, 32)."""
@@ -690,7 +691,8 @@ def stress_config5(steps: int = 3, check_oracle: bool = True, sweep: bool = True
     tbk = statistics.median(b.elapsed_time(c) for _, b, c in ev)
     upd = sum(2.0 * t.N * t.S * wl.R for t, wl in zip(tans, wls))
     out = {"workload": "3d-stress: 101x101x51 S32 R8 + 161x121x61 S32 R32 + 201x201x101 S64 R128",
-           "launch": "one cluster-schedule launch per direction for all three grids (tangent_apply_batch)",
+           "launch": "one persistent launch per direction for all three grids (tangent_apply_batch: merged "
+                     "step-major item order, two items held per CTA)",
            "value": upd / ((tf + tbk) / 1e3), "unit": UNIT, "ms_fwd": round(tf, 3), "ms_bwd": round(tbk, 3),
            "grids": info}
     jp_all = eik.apply_batch(bt, bp)

@@ -311,11 +311,15 @@ int tangent_apply_T(eik_tangent *t, const void *y, int R, int sum_sources,
 
 /*
  * tangent_apply_batch / tangent_apply_T_batch -- J p and J^T y (as tangent_apply with a
- * shared model and tangent_apply_T with the source sum, Sec. 4.4) of up to 4 tangents,
- * e.g. one per grid of a multi-grid workload, in ONE launch of the cluster schedule:
- * thread-block clusters take (tangent, source) units from one queue (tangents in the
- * order given, a tangent's sources by decreasing level count), so condensation DAGs of
- * uneven depth and size run side by side.
+ * shared model and tangent_apply_T with the source sum, Sec. 4.4) of up to 4 distinct
+ * tangents, e.g. one per grid of a multi-grid workload, in ONE traversal launch, so
+ * condensation DAGs of uneven depth and size run side by side.  By default the launch is
+ * the persistent schedule over the work items of all the tangents in one merged order
+ * (step s of every tangent before step s + 1 of any; max(2, item_slots of t[0]) items
+ * held per CTA); if t[0]'s schedule is EIK_SCHED_CLUSTER (or a tangent was built with
+ * items above 64 positions) it is the cluster schedule, whose thread-block clusters take
+ * (tangent, source) units from one queue.  The source sums of J^T follow, one per
+ * tangent.  Results equal the single-tangent calls bit for bit.
  *   t[k]      tangent k (same device for all)
  *   p[k]      device [N_k][R[k]] model vector block of tangent k (shared by its sources)
  *   y[k]      device [S_k][n_rec_k][R[k]] receiver data

@@ -463,6 +463,7 @@ template <typename T, int IM = ITEM_MAX> struct ItemStage {
     int4 it;                     // item descriptor
     int idx;                     // ticket; >= nitems ends the compute warps
     int ebx, eby;                // the item's local edge range
+    int tan, tkt;                // multi-slot schedule: tangent of the item (idx is its item), ticket
 };
 
 // row of the traversal's input for a position of source a, or nullptr (zero input)
@@ -1344,26 +1345,63 @@ __device__ __forceinline__ void prefetch_inputs(const TravParams &P, const ItemS
     }
 }
 
-template <typename T, int V, bool TR, int NS>
-__global__ void __launch_bounds__(256, 4) k_traverse_multi(TravParams P, int G)
+// The tangents of one launch: one (the single-tangent call) or up to CL_MAXTAN (batched
+// applies over several grids).  Tickets run over the items of all of them in a merged
+// step-major order (step s of every tangent before step s + 1 of any), so an item's
+// upstream items still have lower tickets.
+struct MultiBatch {
+    TravParams P[CL_MAXTAN];
+    int G[CL_MAXTAN];            // lanes per position of each tangent
+    int ntan;
+    int nitems;                  // tickets: items of all the tangents
+    const int2 *order;           // ticket -> {tangent, item}; nullptr: one tangent, ticket = item
+    int *ticket;
+};
+
+// descriptor of ticket t into slot S (one thread)
+template <typename T>
+__device__ __forceinline__ void load_desc_multi(const MultiBatch &B, ItemStage<T> &S, int t)
 {
+    S.tkt = t;
+    S.nd = -1;
+    if (t >= B.nitems) return;
+    int k = 0, i = t;
+    if (B.order) {
+        const int2 o = B.order[t];
+        k = o.x;
+        i = o.y;
+    }
+    const TravParams &P = B.P[k];
+    S.tan = k;
+    S.idx = i;
+    S.it = P.items[i];
+    const int2 eb = P.ebeg[i];
+    S.ebx = eb.x;
+    S.eby = eb.y;
+}
+
+template <typename T, int V, bool TR, int NS, bool MT>
+__global__ void __launch_bounds__(256, 4) k_traverse_multi(const __grid_constant__ MultiBatch B)
+{
+    // MT: several tangents (slot k's item belongs to tangent stg[k].tan); else tangent 0
+#define EIK_TAN(S) (MT ? (S).tan : 0)
     __shared__ ItemStage<T> stg[NS];
     __shared__ __align__(8) unsigned long long bar[NS];
     __shared__ int s_pick, s_t;
     const int tid = threadIdx.x;
-    const int nitems = P.nitems;
+    const int ntk = B.nitems;
     const unsigned FULL = 0xffffffffu;
     unsigned ph = 0;                 // bit k: parity of the phase slot k's current copies complete
     unsigned hinted = 0;             // warp 0: bit k set once slot k's input rows were prefetched
     if (tid == 0) {
         for (int k = 0; k < NS; ++k) mbar_init(&bar[k], blockDim.x);
-        for (int k = 0; k < NS; ++k) load_desc(P, stg[k], atomicAdd(P.ticket, 1));
+        for (int k = 0; k < NS; ++k) load_desc_multi(B, stg[k], atomicAdd(B.ticket, 1));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-        if (stg[k].idx < nitems) issue_structure<T>(P, stg[k]);
+        if (stg[k].tkt < ntk) issue_structure<T>(B.P[EIK_TAN(stg[k])], stg[k]);
         cp_async_mbar_arrive(&bar[k]);
     }
     for (;;) {
@@ -1376,7 +1414,7 @@ __global__ void __launch_bounds__(256, 4) k_traverse_multi(TravParams P, int G)
                 unsigned held = 0, landed = 0;
 #pragma unroll
                 for (int k = 0; k < NS; ++k)
-                    if (stg[k].idx < nitems) {
+                    if (stg[k].tkt < ntk) {
                         held |= 1u << k;
                         if (mbar_test(&bar[k], (ph >> k) & 1)) landed |= 1u << k;
                     }
@@ -1389,6 +1427,7 @@ __global__ void __launch_bounds__(256, 4) k_traverse_multi(TravParams P, int G)
                     if (!((landed >> k) & 1)) continue;
                     const ItemStage<T> &S = stg[k];
                     if (S.it.y == 0) continue;          // first step: nothing upstream
+                    const TravParams &P = B.P[EIK_TAN(S)];
                     const int nd = S.nd;
                     const int cnt = nd < 0 ? 1 : nd;
                     for (int j = ((tid - base) % 32 + 32) % 32; j < cnt; j += 32) {
@@ -1409,7 +1448,7 @@ __global__ void __launch_bounds__(256, 4) k_traverse_multi(TravParams P, int G)
                     int best = -1;
 #pragma unroll
                     for (int k = 0; k < NS; ++k)
-                        if (((ready >> k) & 1) && (best < 0 || stg[k].idx < stg[best].idx)) best = k;
+                        if (((ready >> k) & 1) && (best < 0 || stg[k].tkt < stg[best].tkt)) best = k;
                     pick = best;
                     break;
                 }
@@ -1417,13 +1456,13 @@ __global__ void __launch_bounds__(256, 4) k_traverse_multi(TravParams P, int G)
                 const unsigned fresh = landed & ~hinted;
 #pragma unroll
                 for (int k = 0; k < NS; ++k)
-                    if ((fresh >> k) & 1) prefetch_inputs<T, TR>(P, stg[k], tid);
+                    if ((fresh >> k) & 1) prefetch_inputs<T, TR>(B.P[EIK_TAN(stg[k])], stg[k], tid);
                 hinted |= fresh;
                 int stop = 0;
                 if (tid == 0 && (round & 15) == 15) {
-                    if (*(volatile int *)P.err != 0) stop = 1;
-                    else if (global_ns() - t0 > P.timeout_ns) {
-                        if (atomicCAS(P.err, 0, DEV_TIMEOUT) == 0) { P.err[1] = -1; P.err[2] = -1; P.err[3] = -1; }
+                    if (*(volatile int *)B.P[0].err != 0) stop = 1;
+                    else if (global_ns() - t0 > B.P[0].timeout_ns) {
+                        if (atomicCAS(B.P[0].err, 0, DEV_TIMEOUT) == 0) { B.P[0].err[1] = -1; B.P[0].err[2] = -1; B.P[0].err[3] = -1; }
                         stop = 1;
                     }
                 }
@@ -1436,10 +1475,12 @@ __global__ void __launch_bounds__(256, 4) k_traverse_multi(TravParams P, int G)
         const int b = s_pick;
         if (b < 0) break;
         ItemStage<T> &C = stg[b];
+        const int kt = EIK_TAN(C);
+        const TravParams &P = B.P[kt];
         const int4 it = C.it;
         const int i = C.idx;
-        if (tid == 1) s_t = atomicAdd(P.ticket, 1);
-        if (it.z >= 0) run_stage_singletons<T, V, TR>(P, C, nullptr, G);
+        if (tid == 1) s_t = atomicAdd(B.ticket, 1);
+        if (it.z >= 0) run_stage_singletons<T, V, TR>(P, C, nullptr, B.G[kt]);
         else run_block<T, TR>(P, it.x, ~it.z);
         __syncthreads();             // (B) every row of the item written
         if (tid == 32) {
@@ -1447,14 +1488,15 @@ __global__ void __launch_bounds__(256, 4) k_traverse_multi(TravParams P, int G)
             atomicAdd(P.done + (long long)it.x * P.maxL + it.y, 1);
             st_relaxed(P.item_done + i, 1);
         }
-        if (tid == 1) load_desc(P, C, s_t);
+        if (tid == 1) load_desc_multi(B, C, s_t);
         ph ^= 1u << b;
         hinted &= ~(1u << b);
         __syncthreads();             // (C) the slot's next descriptor visible
-        if (C.idx < nitems) issue_structure<T>(P, C);
+        if (C.tkt < ntk) issue_structure<T>(B.P[EIK_TAN(C)], C);
         cp_async_mbar_arrive(&bar[b]);
     }
     cp_async_wait<0>();              // copies of slots never computed land before the CTA exits
+#undef EIK_TAN
 }
 
 // g[j][r] = sum_a cq_a[j] lam_a[j][r] in source order.  FP64 path: FP64 products and
@@ -1857,9 +1899,16 @@ static int launch_traverse(Tangent *t, TravParams &P, int G, cudaStream_t st)
     const int want = t->opts.pass_units > 0 ? t->opts.pass_units : 1;
     if (t->opts.item_slots >= 2 && t->item_max <= ITEM_MAX && want <= 1) {
         // several items held per CTA (input rows read in place, prefetched into L2)
-        void (*mk)(TravParams, int) = t->opts.item_slots >= 4 ? k_traverse_multi<T, V, TR, 4>
-                                      : t->opts.item_slots == 3 ? k_traverse_multi<T, V, TR, 3>
-                                                                : k_traverse_multi<T, V, TR, 2>;
+        void (*mk)(MultiBatch) = t->opts.item_slots >= 4 ? k_traverse_multi<T, V, TR, 4, false>
+                                 : t->opts.item_slots == 3 ? k_traverse_multi<T, V, TR, 3, false>
+                                                           : k_traverse_multi<T, V, TR, 2, false>;
+        MultiBatch B{};
+        B.P[0] = P;
+        B.G[0] = G;
+        B.ntan = 1;
+        B.nitems = P.nitems;
+        B.order = nullptr;
+        B.ticket = P.ticket;
         int per_sm = t->opts.ctas_per_sm;
         if (per_sm <= 0) {
             EIK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mk, threads, 0));
@@ -1870,7 +1919,7 @@ static int launch_traverse(Tangent *t, TravParams &P, int G, cudaStream_t st)
         EIK_CHECK(cudaMemsetAsync(P.done, 0, (size_t)t->S * t->maxL * sizeof(int), st));
         EIK_CHECK(cudaMemsetAsync(P.ticket, 0, sizeof(int), st));
         EIK_CHECK(cudaMemsetAsync(P.item_done, 0, (size_t)std::max(P.nitems, 1) * sizeof(int), st));
-        mk<<<(unsigned)grid, threads, 0, st>>>(P, G);
+        mk<<<(unsigned)grid, threads, 0, st>>>(B);
         EIK_CHECK_LAUNCH();
         return EIK_OK;
     }
@@ -2078,6 +2127,91 @@ static int launch_batch(Tangent *const *ts, int ntan, const TravParams *Ps, cons
     return launch_cluster_u<T, V, TR, 1>(t0, B, units, st);
 }
 
+// ticket -> {tangent, item} of a merged step-major order: runs {tangent, first item, items,
+// first ticket}, in ticket order
+__global__ void k_batch_order(int total, const int4 *__restrict__ runs, int nruns, int2 *__restrict__ order)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int lo = 0, hi = nruns - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (runs[mid].w <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const int4 r = runs[lo];
+    order[t] = make_int2(r.x, r.y + (t - r.w));
+}
+
+// One persistent launch over the items of several tangents (multi-slot kernel): tickets in
+// a merged step-major order, step s of every tangent before step s + 1 of any.
+template <typename T, int V, bool TR>
+static int launch_multi_batch(Tangent *const *ts, int ntan, const TravParams *Ps, const int *R, cudaStream_t st)
+{
+    Tangent *t0 = ts[0];
+    MultiBatch B{};
+    B.ntan = ntan;
+    int smax = 0;
+    for (int k = 0; k < ntan; ++k) {
+        B.P[k] = Ps[k];
+        const int lanes = R[k] / V;
+        int G = 1;
+        while (G < lanes && G < 32) G <<= 1;
+        B.G[k] = G;
+        smax = std::max(smax, ts[k]->maxL);
+    }
+    std::vector<int4> &runs = t0->batch_runs;
+    runs.clear();
+    long long tk = 0;
+    for (int s = 0; s < smax; ++s)
+        for (int k = 0; k < ntan; ++k) {
+            if (s >= ts[k]->maxL) continue;
+            const std::vector<int> &sp = TR ? ts[k]->step_ptr_bwd : ts[k]->step_ptr_fwd;
+            const int n = sp[s + 1] - sp[s];
+            if (n <= 0) continue;
+            runs.push_back(make_int4(k, sp[s], n, (int)tk));
+            tk += n;
+        }
+    if (tk >= (1ll << 31)) { set_error("batch: more than 2^31 - 1 work items"); return EIK_ERR_INVALID; }
+    B.nitems = (int)tk;
+    const size_t need = (size_t)std::max<long long>(tk, 1) * sizeof(int2) + runs.size() * sizeof(int4) + 64;
+    if (need > t0->batch_bytes) {
+        if (t0->batch_buf) cudaFree(t0->batch_buf);
+        t0->batch_buf = nullptr;
+        t0->batch_bytes = 0;
+        EIK_CHECK(cudaMalloc(&t0->batch_buf, need));
+        t0->batch_bytes = need;
+    }
+    int2 *order = reinterpret_cast<int2 *>(t0->batch_buf);
+    int4 *runs_d = reinterpret_cast<int4 *>(reinterpret_cast<char *>(t0->batch_buf) +
+                                            ((size_t)std::max<long long>(tk, 1) * sizeof(int2) + 15) / 16 * 16);
+    if (!runs.empty()) {
+        EIK_CHECK(cudaMemcpyAsync(runs_d, runs.data(), runs.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+        k_batch_order<<<(unsigned)((tk + 255) / 256), 256, 0, st>>>((int)tk, runs_d, (int)runs.size(), order);
+        EIK_CHECK_LAUNCH();
+    }
+    B.order = order;
+    B.ticket = Ps[0].ticket;
+    const int slots = std::max(2, std::min(4, t0->opts.item_slots));
+    void (*mk)(MultiBatch) = slots >= 4 ? k_traverse_multi<T, V, TR, 4, true>
+                             : slots == 3 ? k_traverse_multi<T, V, TR, 3, true> : k_traverse_multi<T, V, TR, 2, true>;
+    const int threads = 256;
+    int per_sm = t0->opts.ctas_per_sm;
+    if (per_sm <= 0) {
+        EIK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mk, threads, 0));
+        per_sm = std::max(per_sm, 1);
+    }
+    long long grid = std::min<long long>((long long)t0->num_sms * per_sm, std::max<long long>(tk, 1));
+    for (int k = 0; k < ntan; ++k) {
+        EIK_CHECK(cudaMemsetAsync(Ps[k].done, 0, (size_t)ts[k]->S * ts[k]->maxL * sizeof(int), st));
+        EIK_CHECK(cudaMemsetAsync(Ps[k].item_done, 0, (size_t)std::max(Ps[k].nitems, 1) * sizeof(int), st));
+    }
+    EIK_CHECK(cudaMemsetAsync(B.ticket, 0, sizeof(int), st));
+    mk<<<(unsigned)grid, threads, 0, st>>>(B);
+    EIK_CHECK_LAUNCH();
+    return EIK_OK;
+}
+
 int traverse_batch(Tangent *const *ts, int ntan, bool TR, const void *const *in, const int *R, void *const *out,
                    int dtype, cudaStream_t st)
 {
@@ -2095,6 +2229,8 @@ int traverse_batch(Tangent *const *ts, int ntan, bool TR, const void *const *in,
         if (t->n_rec == 0) { set_error("batch: tangent %d has no receivers", k); return EIK_ERR_INVALID; }
         if (!aligned16(in[k]) || !aligned16(out[k])) { set_error("device buffers must be 16-byte aligned"); return EIK_ERR_INVALID; }
         if (t->device != ts[0]->device) { set_error("batch: tangents on different devices"); return EIK_ERR_INVALID; }
+        for (int j = 0; j < k; ++j)
+            if (ts[j] == t) { set_error("batch: tangent %d appears twice", k); return EIK_ERR_INVALID; }
         while (R[k] % V) V >>= 1;
         // every right-hand side of every tangent in one pass: the workspace holds them all
         int rc = ensure_workspace(t, (size_t)t->S * t->N * R[k] * esz, (size_t)t->ws_rows * R[k], TR);
@@ -2104,7 +2240,20 @@ int traverse_batch(Tangent *const *ts, int ntan, bool TR, const void *const *in,
         Ps[k] = make_params(ts[k], TR, MODE_J, in[k], TR ? 0 : 1, R[k], R[k], lane_ws(ts[k], TR), nullptr,
                             TR ? nullptr : out[k], TR ? 1 : 0, dtype);
     int rc;
-    if (dtype == EIK_F32) {
+    // the persistent (multi-slot) schedule unless the first tangent asks for the cluster one or
+    // a tangent's items exceed the slot capacity
+    bool persistent = ts[0]->opts.schedule != EIK_SCHED_CLUSTER;
+    for (int k = 0; k < ntan; ++k) persistent = persistent && ts[k]->item_max <= ITEM_MAX;
+    if (persistent) {
+        if (dtype == EIK_F32) {
+            if (V == 4) rc = TR ? launch_multi_batch<float, 4, true>(ts, ntan, Ps, R, st) : launch_multi_batch<float, 4, false>(ts, ntan, Ps, R, st);
+            else if (V == 2) rc = TR ? launch_multi_batch<float, 2, true>(ts, ntan, Ps, R, st) : launch_multi_batch<float, 2, false>(ts, ntan, Ps, R, st);
+            else rc = TR ? launch_multi_batch<float, 1, true>(ts, ntan, Ps, R, st) : launch_multi_batch<float, 1, false>(ts, ntan, Ps, R, st);
+        } else {
+            if (V == 2) rc = TR ? launch_multi_batch<double, 2, true>(ts, ntan, Ps, R, st) : launch_multi_batch<double, 2, false>(ts, ntan, Ps, R, st);
+            else rc = TR ? launch_multi_batch<double, 1, true>(ts, ntan, Ps, R, st) : launch_multi_batch<double, 1, false>(ts, ntan, Ps, R, st);
+        }
+    } else if (dtype == EIK_F32) {
         if (V == 4) rc = TR ? launch_batch<float, 4, true>(ts, ntan, Ps, R, st) : launch_batch<float, 4, false>(ts, ntan, Ps, R, st);
         else if (V == 2) rc = TR ? launch_batch<float, 2, true>(ts, ntan, Ps, R, st) : launch_batch<float, 2, false>(ts, ntan, Ps, R, st);
         else rc = TR ? launch_batch<float, 1, true>(ts, ntan, Ps, R, st) : launch_batch<float, 1, false>(ts, ntan, Ps, R, st);

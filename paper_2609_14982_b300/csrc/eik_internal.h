@@ -234,6 +234,10 @@ struct Tangent {
     int *sync_base[2] = {nullptr, nullptr};
     int sync_steps[2] = {0, 0};
     unsigned *sync_bar = nullptr;
+    // batched persistent launches led by this tangent: the merged ticket order and its runs
+    void *batch_buf = nullptr;
+    size_t batch_bytes = 0;
+    std::vector<int4> batch_runs;
 };
 
 // whether the transpose direction runs on its own launch state

@@ -922,7 +922,7 @@ void free_tangent(Tangent *t)
     void *lane[] = {t->lane_t.ws_vec, t->lane_t.ws_blk, t->lane_t.item_done, t->lane_t.done, t->lane_t.ticket};
     for (void *p : lane) if (p) cudaFree(p);
     void *sync[] = {t->sync_rec[0][0], t->sync_rec[0][1], t->sync_rec[1][0], t->sync_rec[1][1], t->sync_base[0],
-                     t->sync_base[1], t->sync_bar};
+                     t->sync_base[1], t->sync_bar, t->batch_buf};
     for (void *p : sync) if (p) cudaFree(p);
     if (t->params_d) cudaFree((void *)t->params_d);
     for (void *p : t->sweep_w) if (p) cudaFree(p);

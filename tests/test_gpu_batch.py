@@ -1,6 +1,8 @@
 """GPU: several tangents (different grids, source counts, depths and right-hand-side
-counts) traversed in one launch of the cluster schedule give exactly what each tangent
-gives on its own, and match the CPU oracle."""
+counts) traversed in one launch -- of the persistent schedule (a merged step-major item
+order, several items held per CTA) by default, of the cluster schedule when the first
+tangent asks for it -- give exactly what each tangent gives on its own, and match the CPU
+oracle."""
 import numpy as np
 import pytest
 import torch
@@ -46,14 +48,17 @@ def setup(oracle_mod):
     return out
 
 
+@pytest.mark.parametrize("schedule", ["persistent", "cluster"])
 @pytest.mark.parametrize("dtype,Rs", [(torch.float64, (2, 3, 1)), (torch.float32, (8, 16, 4)), (torch.float32, (64, 8, 32))])
-def test_batch_equals_single_and_oracle(oracle_mod, setup, dtype, Rs):
+def test_batch_equals_single_and_oracle(oracle_mod, setup, dtype, Rs, schedule):
     rng = np.random.default_rng(sum(Rs))
     tans = [c[-1] for c in setup]
     ps = [torch.tensor(rng.standard_normal((c[0].N, R)), device=DEV, dtype=dtype) for c, R in zip(setup, Rs)]
     ys = [torch.tensor(rng.standard_normal((len(c[2]), len(c[3]), R)), device=DEV, dtype=dtype) for c, R in zip(setup, Rs)]
+    tans[0].tune(schedule=eik.SCHED_CLUSTER if schedule == "cluster" else eik.SCHED_PERSISTENT)
     jp = eik.apply_batch(tans, ps)
     jt = eik.apply_T_batch(tans, ys)
+    tans[0].tune(schedule=eik.SCHED_PERSISTENT)
     tol = 1e-10 if dtype == torch.float64 else 1e-5
     for (g, s, srcs, rec, ot, tan), p, y, a, b in zip(setup, ps, ys, jp, jt):
         _, single = tan.apply(p, shared_model=True)
@@ -72,3 +77,11 @@ def test_batch_rejects_bad_arguments(setup):
     p = torch.zeros((setup[0][0].N, 4), device=DEV)
     with pytest.raises(ValueError):
         eik.apply_batch(tans * 2, [p] * 6)
+
+
+def test_batch_rejects_a_repeated_tangent(setup):
+    """Each tangent keeps its own counters: the same tangent twice in one batch is refused."""
+    tans = [c[-1] for c in setup]
+    ps = [torch.zeros((setup[0][0].N, 4), device=DEV)] * 2
+    with pytest.raises(eik.EikError):
+        eik.apply_batch([tans[0], tans[0]], ps)
