@@ -136,8 +136,8 @@ typedef struct {
     int item_slots;            /* persistent schedule: work items a CTA holds at once, 1 (default)
                                   or 2..4; with several, each item's structure lands in its own
                                   shared-memory slot and the CTA computes whichever held item
-                                  has its upstream items done first (64-position items, one
-                                  right-hand-side vector per thread) */
+                                  has its upstream items done first (one right-hand-side vector
+                                  per thread; items above 64 positions use two slots) */
 } eik_opts;
 
 typedef struct {

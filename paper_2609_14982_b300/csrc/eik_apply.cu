@@ -1330,8 +1330,8 @@ __device__ __forceinline__ bool mbar_test(unsigned long long *b, unsigned parity
 }
 
 // input rows of a landed slot into L2 (lanes of warp 0)
-template <typename T, bool TR>
-__device__ __forceinline__ void prefetch_inputs(const TravParams &P, const ItemStage<T> &S, int lane)
+template <typename T, bool TR, int IM>
+__device__ __forceinline__ void prefetch_inputs(const TravParams &P, const ItemStage<T, IM> &S, int lane)
 {
     if (S.it.z < 0) return;
     const int np = S.it.w - S.it.z;
@@ -1359,8 +1359,8 @@ struct MultiBatch {
 };
 
 // descriptor of ticket t into slot S (one thread)
-template <typename T>
-__device__ __forceinline__ void load_desc_multi(const MultiBatch &B, ItemStage<T> &S, int t)
+template <typename T, int IM>
+__device__ __forceinline__ void load_desc_multi(const MultiBatch &B, ItemStage<T, IM> &S, int t)
 {
     S.tkt = t;
     S.nd = -1;
@@ -1380,12 +1380,12 @@ __device__ __forceinline__ void load_desc_multi(const MultiBatch &B, ItemStage<T
     S.eby = eb.y;
 }
 
-template <typename T, int V, bool TR, int NS, bool MT>
+template <typename T, int V, bool TR, int NS, bool MT, int IM = ITEM_MAX>
 __global__ void __launch_bounds__(256, 4) k_traverse_multi(const __grid_constant__ MultiBatch B)
 {
     // MT: several tangents (slot k's item belongs to tangent stg[k].tan); else tangent 0
 #define EIK_TAN(S) (MT ? (S).tan : 0)
-    __shared__ ItemStage<T> stg[NS];
+    __shared__ ItemStage<T, IM> stg[NS];
     __shared__ __align__(8) unsigned long long bar[NS];
     __shared__ int s_pick, s_t;
     const int tid = threadIdx.x;
@@ -1425,7 +1425,7 @@ __global__ void __launch_bounds__(256, 4) k_traverse_multi(const __grid_constant
 #pragma unroll
                 for (int k = 0; k < NS; ++k) {
                     if (!((landed >> k) & 1)) continue;
-                    const ItemStage<T> &S = stg[k];
+                    const ItemStage<T, IM> &S = stg[k];
                     if (S.it.y == 0) continue;          // first step: nothing upstream
                     const TravParams &P = B.P[EIK_TAN(S)];
                     const int nd = S.nd;
@@ -1456,7 +1456,7 @@ __global__ void __launch_bounds__(256, 4) k_traverse_multi(const __grid_constant
                 const unsigned fresh = landed & ~hinted;
 #pragma unroll
                 for (int k = 0; k < NS; ++k)
-                    if ((fresh >> k) & 1) prefetch_inputs<T, TR>(B.P[EIK_TAN(stg[k])], stg[k], tid);
+                    if ((fresh >> k) & 1) prefetch_inputs<T, TR, IM>(B.P[EIK_TAN(stg[k])], stg[k], tid);
                 hinted |= fresh;
                 int stop = 0;
                 if (tid == 0 && (round & 15) == 15) {
@@ -1474,7 +1474,7 @@ __global__ void __launch_bounds__(256, 4) k_traverse_multi(const __grid_constant
         __syncthreads();             // (A) the picked item's upstream rows are complete
         const int b = s_pick;
         if (b < 0) break;
-        ItemStage<T> &C = stg[b];
+        ItemStage<T, IM> &C = stg[b];
         const int kt = EIK_TAN(C);
         const TravParams &P = B.P[kt];
         const int4 it = C.it;
@@ -1897,9 +1897,11 @@ static int launch_traverse(Tangent *t, TravParams &P, int G, cudaStream_t st)
     // item is bound by dependent-instruction and memory latency, not by instruction count)
     const int lanes = P.R / V;
     const int want = t->opts.pass_units > 0 ? t->opts.pass_units : 1;
-    if (t->opts.item_slots >= 2 && t->item_max <= ITEM_MAX && want <= 1) {
-        // several items held per CTA (input rows read in place, prefetched into L2)
-        void (*mk)(MultiBatch) = t->opts.item_slots >= 4 ? k_traverse_multi<T, V, TR, 4, false>
+    if (t->opts.item_slots >= 2 && want <= 1) {
+        // several items held per CTA (input rows read in place, prefetched into L2); items of
+        // more than 64 positions (few right-hand sides) take two slots of the large capacity
+        void (*mk)(MultiBatch) = t->item_max > ITEM_MAX ? k_traverse_multi<T, V, TR, 2, false, ITEM_CAP>
+                                 : t->opts.item_slots >= 4 ? k_traverse_multi<T, V, TR, 4, false>
                                  : t->opts.item_slots == 3 ? k_traverse_multi<T, V, TR, 3, false>
                                                            : k_traverse_multi<T, V, TR, 2, false>;
         MultiBatch B{};

@@ -1,7 +1,7 @@
 """GPU: tangents built with items above 64 positions (eik_opts.chunk up to 256, the form for
 few right-hand sides) give the same J p and J^T y bit for bit as the default items, in the
-persistent schedule (the large-item kernel instance) and the cluster schedule; the
-per-level schedules refuse them with EIK_ERR_INVALID."""
+persistent schedule (the large-item kernel instance, one or two items held per CTA) and the
+cluster schedule; the per-level schedules refuse them with EIK_ERR_INVALID."""
 import numpy as np
 import pytest
 import torch
@@ -37,11 +37,12 @@ def _run(case, chunk, dtype, R, **opts):
     return dT, d, gs
 
 
+@pytest.mark.parametrize("slots", [0, 2])
 @pytest.mark.parametrize("chunk", [128, 256])
 @pytest.mark.parametrize("dtype,R", [(torch.float64, 1), (torch.float32, 1), (torch.float64, 4), (torch.float32, 16)])
-def test_large_items_equal_default_items(case, chunk, dtype, R):
+def test_large_items_equal_default_items(case, chunk, dtype, R, slots):
     ref = _run(case, 0, dtype, R)
-    got = _run(case, chunk, dtype, R)
+    got = _run(case, chunk, dtype, R, item_slots=slots)
     for u, v in zip(ref, got):
         assert torch.equal(u, v)
 
