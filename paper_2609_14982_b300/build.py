@@ -59,7 +59,7 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
     if not force and os.path.exists(lib_out) and os.path.exists(stamp) and open(stamp).read().strip() == dig:
         return lib_out
     os.makedirs(build_dir, exist_ok=True)
-    objs = []
+    objs, cmds = [], []
     for src in _sources():
         obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
@@ -69,8 +69,13 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
         if verbose:
             cmd.insert(-4, "-Xptxas=-v")
             print(" ".join(cmd), flush=True)
-        subprocess.check_call(cmd)
+        cmds.append(cmd)
         objs.append(obj)
+    # the translation units compile independently: run them side by side
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=max(1, min(len(cmds), os.cpu_count() or 1))) as pool:
+        for f in [pool.submit(subprocess.check_call, c) for c in cmds]:
+            f.result()
     tmp = lib_out + f".tmp{os.getpid()}"
     subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
     os.replace(tmp, lib_out)
