@@ -393,8 +393,10 @@ int tangent_tune(eik_tangent *t, const eik_opts *opts);
  * for before (source, step), so that wait can never be satisfied, and makes every item
  * wait for its whole previous level while a hold is in place: the next persistent
  * tangent_apply / tangent_solve ends after about wait_timeout_s and tangent_status
- * returns EIK_ERR_TIMEOUT.  source < 0 undoes every hold.  No fault is raised on the
- * device; the context stays usable.
+ * returns EIK_ERR_TIMEOUT.  In the level-synchronous schedule a hold makes CTA 0 skip its
+ * arrival at global step `step` (either direction), so every CTA's barrier wait runs out
+ * the same way.  source < 0 undoes every hold.  No fault is raised on the device; the
+ * context stays usable.
  */
 int tangent_debug_hold(eik_tangent *t, int source, int step);
 

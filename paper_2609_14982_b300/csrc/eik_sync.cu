@@ -391,7 +391,7 @@ __device__ __forceinline__ void sy_prefetch(const TravParams &P, const SyRec<T> 
 template <typename T, int V, bool TR, int NT, int ILP>
 __global__ void __launch_bounds__(NT, 1)
     k_traverse_sync(const __grid_constant__ TravParams P, const SyRec<T> *__restrict__ recs,
-                    const int *__restrict__ step_base, int nsteps, unsigned *bar)
+                    const int *__restrict__ step_base, int nsteps, unsigned *bar, int hold_step)
 {
     extern __shared__ __align__(16) unsigned char ring_raw[];     // 3 slots x SY_UMAX records, slice table
     SyRec<T> *ring = reinterpret_cast<SyRec<T> *>(ring_raw);
@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(NT, 1)
         if (b1 > b0) sy_blocks<T, V, TR>(P, recs, b0, b1);
         // ---- arrive: every store of this CTA for step s, then the counter
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && !(s == hold_step && blockIdx.x == 0)) {   // (a test hold: CTA 0 skips one arrival)
             asm volatile("fence.acq_rel.gpu;" ::: "memory");
             asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
         }
@@ -608,7 +608,7 @@ static int launch_sync_t(Tangent *t, const TravParams &P, cudaStream_t st)
     }
     // one CTA per SM: 1024 threads with one unit in flight each (default), or fewer threads
     // with 2 or 4 units in flight each (pass_units)
-    void (*kern)(TravParams, const SyRec<T> *, const int *, int, unsigned *) = k_traverse_sync<T, V, TR, 1024, 1>;
+    void (*kern)(TravParams, const SyRec<T> *, const int *, int, unsigned *, int) = k_traverse_sync<T, V, TR, 1024, 1>;
     int threads = 1024;
     if (t->opts.pass_units == 2) { kern = k_traverse_sync<T, V, TR, 768, 2>; threads = 768; }
     else if (t->opts.pass_units == 3) { kern = k_traverse_sync<T, V, TR, 1024, 2>; threads = 1024; }
@@ -635,8 +635,11 @@ static int launch_sync_t(Tangent *t, const TravParams &P, cudaStream_t st)
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
+    // while a test hold (tangent_debug_hold) is in place, CTA 0 skips its arrival at one step,
+    // so every CTA's bounded barrier wait runs out
+    const int hold = t->holds.empty() ? -1 : (int)std::min<long long>(t->holds[0] % t->maxL, t->sync_steps[d] - 1);
     EIK_CHECK(cudaLaunchKernelEx(&cfg, kern, P, (const SyRec<T> *)t->sync_rec[d][f], (const int *)t->sync_base[d],
-                                 t->sync_steps[d], bar));
+                                 t->sync_steps[d], bar, hold));
     return EIK_OK;
 }
 

@@ -192,3 +192,23 @@ def test_sync_stress_grid_blocks(oracle_mod):
     pn, yn = p.double().cpu().numpy(), y.double().cpu().numpy()
     assert rel_err(jp.double().cpu().numpy(), oracle_mod.J(otans, wl.s, wl.rec, pn)) <= 1e-5
     assert rel_err(gt.double().cpu().numpy(), oracle_mod.JT(otans, wl.s, wl.rec, yn)) <= 1e-5
+
+
+def test_sync_barrier_timeout_reported_and_context_survives(case):
+    """A grid barrier that cannot complete (a test hold makes one CTA skip its arrival) ends
+    every CTA's bounded wait with EIK_ERR_TIMEOUT; the next traversal on the same context is
+    correct again."""
+    g, Ts, s, srcs, _ = case("table3-41x41x25")
+    tan = _tangent(g, Ts, s, srcs, wait_timeout_s=0.25)
+    q = torch.randn((len(srcs), g.N, 2), device=DEV, dtype=torch.float64)
+    good = tan.solve(q).clone()
+    tan.status()
+    tan.debug_hold(0, 3)
+    tan.solve(q)
+    with pytest.raises(eik.EikError) as e:
+        tan.status()
+    assert e.value.code == -5
+    tan.debug_hold(-1, -1)
+    again = tan.solve(q)
+    tan.status()
+    assert torch.equal(again, good)
